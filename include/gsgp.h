@@ -1,0 +1,268 @@
+/*
+ * gsgp.h - C ABI of the GB300 (sm_103a) Geometric Semantic GP library.
+ *
+ * The library runs the data-parallel hot path of GSGP for symbolic
+ * regression (Trujillo et al., "GSGP-CUDA: a CUDA framework for Geometric
+ * Semantic Genetic Programming", Sec. 2 and Algorithm 1) on one GPU:
+ *   - program generation for the population P and the random-tree pool R,
+ *   - interpretation of every program over all fitness cases (semantics),
+ *   - per generation: tournament selection, geometric semantic mutation
+ *     offspring = parent + ms * (sigma(R_a) - sigma(R_b)) over the semantic
+ *     vectors, fused with the training and test RMSE of every offspring,
+ *     survival with elitism and an ancestry trace on the device,
+ *   - reconstruction of the best individual from the trace and its
+ *     evaluation on new cases.
+ *
+ * Conventions shared by every call:
+ *   - Every call returns a gsgp_status; nothing throws or aborts across the
+ *     ABI.  On failure the context keeps a message (gsgp_last_error) and
+ *     stays destroyable.  GSGP_E_CUDA means a CUDA runtime error.
+ *   - Inputs are copied: the caller keeps ownership of every pointer it
+ *     passes.  Outputs go to caller-allocated buffers.
+ *   - Host pointers are ordinary (pageable or pinned) CPU memory.  Device
+ *     pointers are CUDA global memory of the context's device.
+ *   - All device work is ordered on config.stream (a cudaStream_t; NULL
+ *     means the legacy default stream).  Calls that return host data
+ *     synchronise that stream before returning.
+ *   - Call order: create -> load -> init -> evolve* -> best_trace / predict.
+ *     init may be called again to restart the run; load again to replace
+ *     the data (then init).  Out-of-order calls return GSGP_E_STATE.
+ *   - A context is not thread-safe; distinct contexts are independent.
+ *
+ * Randomness: Philox4x32-10 (Salmon et al., SC'11), key = (seed low 32 bits,
+ * seed high 32 bits), counter = (block, individual, generation-or-purpose,
+ * run).  Initialisation streams use 0x80000000 | purpose (1 = population,
+ * 2 = random trees); generation g uses g.  Identical draws are reproduced by
+ * an independent CPU implementation.
+ */
+#ifndef GSGP_H
+#define GSGP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct gsgp_ctx gsgp_ctx;
+
+typedef enum {
+  GSGP_OK = 0,
+  GSGP_E_INVALID = 1,  /* bad argument, size, configuration or non-finite input */
+  GSGP_E_STATE = 2,    /* call out of order (e.g. evolve before init) */
+  GSGP_E_OOM = 3,      /* device or host allocation failed */
+  GSGP_E_CUDA = 4,     /* CUDA runtime error; message in gsgp_last_error */
+  GSGP_E_TIMEOUT = 5,  /* a bounded device-side wait gave up */
+  GSGP_E_NUMERIC = 6   /* numerical failure (reserved) */
+} gsgp_status;
+
+/* Gene encoding of the linear (postfix) program representation (Sec. 2.2,
+ * "Initialization"): function set {+, -, x, protected /}; terminals are
+ * input features and ephemeral random constants.  A gene is an int32:
+ * GSGP_OP_ADD..GSGP_OP_DIV are functions; GSGP_OP_CONST takes its value from
+ * the parallel float array; GSGP_OP_VAR | (f << 8) reads feature f;
+ * GSGP_GENE_PAD (-1) fills a program's row after its last gene. */
+enum {
+  GSGP_OP_ADD = 0,
+  GSGP_OP_SUB = 1,
+  GSGP_OP_MUL = 2,
+  GSGP_OP_DIV = 3,   /* protected: |b| < protect_eps gives 1 */
+  GSGP_OP_CONST = 4,
+  GSGP_OP_VAR = 5,
+  GSGP_GENE_PAD = -1
+};
+
+enum { GSGP_SIGMA_F32 = 0, GSGP_SIGMA_BF16 = 1 };
+enum { GSGP_POOL_POPULATION = 0, GSGP_POOL_RANDOM = 1 };
+
+/* Optional device allocator.  alloc returns device memory of at least
+ * `bytes` bytes usable on `stream` (NULL on failure -> GSGP_E_OOM); free
+ * releases it.  When NULL the library uses cudaMallocAsync/cudaFreeAsync. */
+typedef void *(*gsgp_alloc_fn)(void *user, size_t bytes, void *stream);
+typedef void (*gsgp_free_fn)(void *user, void *ptr, void *stream);
+
+typedef struct {
+  uint32_t struct_size;        /* = sizeof(gsgp_config); ABI versioning */
+  uint64_t seed;               /* Philox key */
+  uint32_t run;                /* Philox counter word 3: independent runs */
+  int32_t pop_size;            /* m, 2 .. 65536 */
+  int32_t n_random_trees;      /* r, 1 .. 65536 */
+  int32_t pop_min_depth, pop_max_depth;  /* ramped half-and-half depths, 0..10 */
+  int32_t rt_min_depth, rt_max_depth;
+  float const_lo, const_hi;    /* ephemeral random constants in [lo, hi) */
+  float p_grow_function;       /* grow method: P(function) below the root */
+  float p_feature_given_terminal; /* P(feature) for a terminal; else constant */
+  float protect_eps;           /* protected division threshold (strict <) */
+  float ms;                    /* mutation step */
+  int32_t ms_mode;             /* 0: fixed ms; 1: ms * U[0,1) per mutation */
+  int32_t tournament_size;     /* 0: slot i mutates parent i (no selection) */
+  int32_t elitism;             /* 1: keep the best of parents and offspring */
+  int32_t sigma_dtype;         /* GSGP_SIGMA_F32 or GSGP_SIGMA_BF16 storage of sigma(R) */
+  void *stream;                /* cudaStream_t for all device work */
+  gsgp_alloc_fn alloc;         /* optional device allocator (see above) */
+  gsgp_free_fn free;
+  void *alloc_user;
+} gsgp_config;
+
+/* Fill *cfg with defaults: seed 1, run 0, m = 1024, r = 1024, depths 2-6,
+ * constants in [-1, 1), p_grow 0.5, p_feature 7/9, protect_eps 1e-3,
+ * ms 0.1 fixed, tournament 4, elitism on, float32 sigma, NULL stream and
+ * allocator.  No CUDA call. */
+void gsgp_config_default(gsgp_config *cfg);
+
+/* Reason *cfg would be rejected by gsgp_create, or "" when it is valid.
+ * Static string; no CUDA call. */
+const char *gsgp_config_error(const gsgp_config *cfg);
+
+/* Validate *cfg and create a context (host memory only; no CUDA call).
+ * Errors: GSGP_E_INVALID (NULL pointers, struct_size mismatch, sizes or
+ * probabilities out of range), GSGP_E_OOM. */
+gsgp_status gsgp_create(const gsgp_config *cfg, gsgp_ctx **out);
+
+/* Fitness cases (Sec. 2: fc_j = (x_j, t_j), x_j in R^l) from HOST memory in
+ * the paper's file layout (Sec. 3.3): X_* row-major (cases x n_features)
+ * float32, y_* one float32 target per case.  Training cases drive selection;
+ * test cases (n_test may be 0, pointers then NULL) are evaluated for every
+ * individual.  The library copies them to the device, stored feature-major.
+ * Errors: GSGP_E_INVALID (n_train < 1, n_features < 1 or > 65535,
+ * NULL data, any non-finite value), GSGP_E_OOM, GSGP_E_CUDA. */
+gsgp_status gsgp_load(gsgp_ctx *ctx, const float *X_train, const float *y_train,
+                      int64_t n_train, int32_t n_features, const float *X_test,
+                      const float *y_test, int64_t n_test);
+
+/* As gsgp_load with DEVICE pointers (same layouts).  Non-finite values are
+ * detected on the device (GSGP_E_INVALID). */
+gsgp_status gsgp_load_device(gsgp_ctx *ctx, const float *X_train, const float *y_train,
+                             int64_t n_train, int32_t n_features, const float *X_test,
+                             const float *y_test, int64_t n_test);
+
+/* Initialisation of Algorithm 1: CreatePopulation for P (m programs) and R
+ * (r programs), ComputeSemantics of both over all cases (random trees
+ * wrapped by the logistic function, Sec. 2), ComputeFitness of P.  Resets
+ * the generation counter and the trace.  Errors: GSGP_E_STATE (no data),
+ * GSGP_E_OOM, GSGP_E_CUDA. */
+gsgp_status gsgp_init(gsgp_ctx *ctx);
+
+/* Run `generations` generations of the loop of Algorithm 1 (GSM, fitness of
+ * the offspring, survival with elitism), continuing from the current one.
+ * best_train_rmse / best_test_rmse (nullable HOST arrays of `generations`
+ * doubles) receive, per generation, the training and test RMSE of the best
+ * individual after survival (the paper's two output series, Sec. 3.3);
+ * when both are NULL the call does not synchronise.
+ * Errors: GSGP_E_STATE (before init), GSGP_E_INVALID (generations < 0),
+ * GSGP_E_OOM, GSGP_E_CUDA. */
+gsgp_status gsgp_evolve(gsgp_ctx *ctx, int32_t generations, double *best_train_rmse,
+                        double *best_test_rmse);
+
+/* The best individual ("Return: best individual found", Algorithm 1) as a
+ * model: its generation-0 ancestor in P plus one coefficient per random
+ * tree, obtained by walking the ancestry trace back from the best slot
+ * (each mutation adds +ms to rt1's coefficient and -ms to rt2's).  The model
+ * is y(x) = P_ancestor(x) + sum_k coef[k] * q(sigma(R_k(x))), where q rounds
+ * to bfloat16 when sigma_dtype is BF16 and is the identity otherwise.
+ * Size query: set the pointer fields to NULL to receive only the sizes.
+ * All pointers are HOST buffers owned by the caller. */
+typedef struct {
+  uint32_t struct_size;     /* in: sizeof(gsgp_trace) */
+  int32_t best_slot;        /* out: population slot of the best individual */
+  double best_train_rmse;   /* out */
+  double best_test_rmse;    /* out */
+  int32_t ancestor;         /* out: index of the ancestor in P */
+  int32_t ancestor_length;  /* out: genes of the ancestor */
+  int32_t max_genes;        /* out: row length of P programs */
+  int32_t *ancestor_genes;  /* in/out, nullable: max_genes int32 */
+  float *ancestor_consts;   /* in/out, nullable: max_genes float */
+  int32_t n_generations;    /* out: length of the lineage (generations run) */
+  int32_t *lineage_parent;  /* in/out, nullable: per generation g, the slot at g-1 */
+  int32_t *lineage_rt1;     /* in/out, nullable: -1 for an elite copy */
+  int32_t *lineage_rt2;
+  float *lineage_ms;
+  int32_t n_random_trees;   /* out: r */
+  double *coef;             /* in/out, nullable: r coefficients */
+  int32_t rt_max_genes;     /* out: row length of R programs */
+  int32_t *rt_genes;        /* in/out, nullable: r * rt_max_genes */
+  float *rt_consts;         /* in/out, nullable: r * rt_max_genes */
+  int32_t *rt_lengths;      /* in/out, nullable: r */
+  int32_t sigma_dtype;      /* out */
+} gsgp_trace;
+
+/* Errors: GSGP_E_STATE (before init), GSGP_E_INVALID, GSGP_E_CUDA. */
+gsgp_status gsgp_best_trace(gsgp_ctx *ctx, gsgp_trace *out);
+
+/* Evaluate the best model (see gsgp_trace) in float64 on n new cases:
+ * X row-major (n x n_features) float32 HOST, y_out n doubles HOST.
+ * Errors: GSGP_E_STATE (before init), GSGP_E_INVALID (n < 0, NULL with
+ * n > 0, non-finite X), GSGP_E_OOM, GSGP_E_CUDA. */
+gsgp_status gsgp_predict(gsgp_ctx *ctx, const float *X, int64_t n, double *y_out);
+
+/* As gsgp_predict with DEVICE pointers; does not synchronise. */
+gsgp_status gsgp_predict_device(gsgp_ctx *ctx, const float *X, int64_t n, double *y_out);
+
+/* Last error message of ctx ("" if none); valid until the next call. */
+const char *gsgp_last_error(const gsgp_ctx *ctx);
+
+/* Release every resource of ctx (NULL is ignored).  Synchronises its stream. */
+void gsgp_destroy(gsgp_ctx *ctx);
+
+/* ---- Introspection: sizes, programs, semantics, fitness, trace ----------- */
+
+typedef struct {
+  uint32_t struct_size;     /* in: sizeof(gsgp_info) */
+  int32_t state;            /* 0 created, 1 loaded, 2 initialised */
+  int32_t n_features;
+  int64_t n_train, n_test, n_cases;   /* n_cases = n_train + n_test */
+  int64_t n_cases_padded;             /* row stride of semantic matrices */
+  int32_t pop_size, n_random_trees;
+  int32_t pop_max_genes, rt_max_genes;
+  int32_t generation;                 /* generations run since init */
+  int32_t evolve_tile_cases;          /* cases per tile of the generation kernel */
+  int32_t evolve_offspring_per_cta;
+  int64_t kernel_launches;            /* library kernels launched since create */
+  int64_t device_bytes;               /* device memory held by the context */
+} gsgp_info;
+
+gsgp_status gsgp_get_info(gsgp_ctx *ctx, gsgp_info *out);
+
+/* Programs of a pool (GSGP_POOL_POPULATION or GSGP_POOL_RANDOM) as
+ * generated by init: genes/consts HOST (count x max_genes), lengths HOST
+ * (count).  Any pointer may be NULL. */
+gsgp_status gsgp_get_programs(gsgp_ctx *ctx, int32_t pool, int32_t *genes, float *consts,
+                              int32_t *lengths);
+
+/* Semantic vectors of rows [row0, row0 + rows) over all n_cases cases, as
+ * float32 into HOST out (rows x n_cases): the current population
+ * (GSGP_POOL_POPULATION, slot order) or the sigma-wrapped random trees
+ * (GSGP_POOL_RANDOM; BF16 storage is widened exactly). */
+gsgp_status gsgp_get_semantics(gsgp_ctx *ctx, int32_t pool, int32_t row0, int32_t rows,
+                               float *out);
+
+/* Training and test RMSE of the current population (HOST, m doubles each;
+ * either may be NULL). */
+gsgp_status gsgp_get_fitness(gsgp_ctx *ctx, double *train, double *test);
+
+/* Trace entries of generations [g0, g0 + count): HOST arrays of count * m,
+ * generation-major; rt1 = rt2 = -1 and ms = 0 mark an elite copy. */
+gsgp_status gsgp_get_trace(gsgp_ctx *ctx, int32_t g0, int32_t count, int32_t *parent,
+                           int32_t *rt1, int32_t *rt2, float *ms);
+
+/* Kernel timing of the generation kernel.  When enabled, gsgp_evolve
+ * records CUDA events around every launch of the fused generation kernel on
+ * config.stream; gsgp_kernel_times then synchronises and returns the
+ * durations (ms) of the most recent min(cap, n) launches, oldest first, and
+ * clears them.  *n_out receives the count. */
+gsgp_status gsgp_set_kernel_timing(gsgp_ctx *ctx, int32_t enabled);
+gsgp_status gsgp_kernel_times(gsgp_ctx *ctx, float *ms, int32_t cap, int32_t *n_out);
+
+/* Philox4x32-10 words [0, n_words) of the stream (individual,
+ * gen_or_purpose, run) under key `seed`, computed on the GPU on `stream` and
+ * copied to HOST `out`.  Errors: GSGP_E_INVALID, GSGP_E_CUDA. */
+gsgp_status gsgp_rng_words(uint64_t seed, uint32_t run, uint32_t gen_or_purpose,
+                           uint32_t individual, int32_t n_words, uint32_t *out,
+                           void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GSGP_H */

@@ -199,3 +199,67 @@ def postfix_to_tree(genes, consts):
             st.append((names[op], a, b))
     assert len(st) == 1
     return st[0]
+
+
+U32 = 2.0 ** -24          # unit roundoff of float32 round-to-nearest
+
+
+def eval_postfix_fp32_bound(genes, consts, X, protect_eps: float = 1e-3):
+    """Exact (float64) value of a program and a first-order bound on the
+    error of evaluating it in float32 arithmetic, every operation rounded
+    once to nearest (running error analysis, Wilkinson).
+
+    For operands a, b carrying errors ea, eb:
+      a +- b : ea + eb
+      a * b  : |a| eb + |b| ea + ea eb
+      a / b  : (ea + |a/b| eb) / (|b| - eb)
+    plus u (|r| + e) for the rounding of the result r.  The bound is
+    infinite where float32 could take the other branch of protected division
+    (|b| within its error of eps) or where a magnitude exceeds 1e38 (float32
+    overflow), i.e. where the two precisions may legitimately disagree.
+    Returns (value (n,), bound (n,)).
+    """
+    eps = float(np.float32(protect_eps))
+    n = X.shape[1]
+    stack = []
+    with np.errstate(all="ignore"):
+        for g, c in zip(genes, consts):
+            g = int(g)
+            if g == PAD:
+                break
+            op = g & 0xFF
+            if op == OP_VAR:
+                stack.append((X[g >> 8].astype(np.float64), np.zeros(n)))
+                continue
+            if op == OP_CONST:
+                stack.append((np.full(n, float(c)), np.zeros(n)))
+                continue
+            b, eb = stack.pop()
+            a, ea = stack.pop()
+            if op == OP_ADD:
+                r, e = a + b, ea + eb
+            elif op == OP_SUB:
+                r, e = a - b, ea + eb
+            elif op == OP_MUL:
+                r, e = a * b, np.abs(a) * eb + np.abs(b) * ea + ea * eb
+            else:
+                small = np.abs(b) < eps
+                r = np.where(small, 1.0, a / np.where(small, 1.0, b))
+                den = np.abs(b) - eb
+                e = np.where(small, 0.0, (ea + np.abs(r) * eb) / np.where(den > 0, den, 1.0))
+                ab = np.abs(b)
+                flip = np.where(small, ab + eb >= eps, ab - eb < eps) | (~small & (den <= 0))
+                e = np.where(flip, np.inf, e)
+            e = e + U32 * (np.abs(r) + e)
+            e = np.where(np.abs(r) > 1e38, np.inf, e)
+            e = np.where(np.isfinite(r), e, np.inf)
+            stack.append((r, e))
+    if len(stack) != 1:
+        raise ValueError("program is not well-formed postfix")
+    return stack[0]
+
+
+def sigma_fp32_bound(v_bound):
+    """Error bound of sigma computed in float32 from an argument with error
+    v_bound: |sigma'| <= 1/4, plus a few roundings of a value in [0, 1]."""
+    return np.asarray(v_bound) / 4.0 + 8 * U32

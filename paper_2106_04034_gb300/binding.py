@@ -1,0 +1,350 @@
+"""ctypes binding of libgsgp.so (argument marshalling only).
+
+Every function of include/gsgp.h is exposed under the same name on ``lib``;
+``Run`` wraps one context.  No step of the method runs in Python: arrays
+are handed to the library as pointers (numpy arrays for host buffers, torch
+CUDA tensors for device buffers), and a non-OK status raises GsgpError.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Optional
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "_lib", "libgsgp.so")
+
+STATUS = {0: "GSGP_OK", 1: "GSGP_E_INVALID", 2: "GSGP_E_STATE", 3: "GSGP_E_OOM",
+          4: "GSGP_E_CUDA", 5: "GSGP_E_TIMEOUT", 6: "GSGP_E_NUMERIC"}
+OK, E_INVALID, E_STATE, E_OOM, E_CUDA, E_TIMEOUT, E_NUMERIC = range(7)
+OP_ADD, OP_SUB, OP_MUL, OP_DIV, OP_CONST, OP_VAR, GENE_PAD = 0, 1, 2, 3, 4, 5, -1
+SIGMA_F32, SIGMA_BF16 = 0, 1
+POOL_POPULATION, POOL_RANDOM = 0, 1
+
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p, C.c_void_p)
+
+
+class GsgpError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Config(C.Structure):
+    _fields_ = [
+        ("struct_size", C.c_uint32), ("seed", C.c_uint64), ("run", C.c_uint32),
+        ("pop_size", C.c_int32), ("n_random_trees", C.c_int32),
+        ("pop_min_depth", C.c_int32), ("pop_max_depth", C.c_int32),
+        ("rt_min_depth", C.c_int32), ("rt_max_depth", C.c_int32),
+        ("const_lo", C.c_float), ("const_hi", C.c_float),
+        ("p_grow_function", C.c_float), ("p_feature_given_terminal", C.c_float),
+        ("protect_eps", C.c_float), ("ms", C.c_float), ("ms_mode", C.c_int32),
+        ("tournament_size", C.c_int32), ("elitism", C.c_int32), ("sigma_dtype", C.c_int32),
+        ("stream", C.c_void_p), ("alloc", ALLOC_FN), ("free", FREE_FN),
+        ("alloc_user", C.c_void_p),
+    ]
+
+
+class Trace(C.Structure):
+    _fields_ = [
+        ("struct_size", C.c_uint32), ("best_slot", C.c_int32),
+        ("best_train_rmse", C.c_double), ("best_test_rmse", C.c_double),
+        ("ancestor", C.c_int32), ("ancestor_length", C.c_int32), ("max_genes", C.c_int32),
+        ("ancestor_genes", C.POINTER(C.c_int32)), ("ancestor_consts", C.POINTER(C.c_float)),
+        ("n_generations", C.c_int32),
+        ("lineage_parent", C.POINTER(C.c_int32)), ("lineage_rt1", C.POINTER(C.c_int32)),
+        ("lineage_rt2", C.POINTER(C.c_int32)), ("lineage_ms", C.POINTER(C.c_float)),
+        ("n_random_trees", C.c_int32), ("coef", C.POINTER(C.c_double)),
+        ("rt_max_genes", C.c_int32), ("rt_genes", C.POINTER(C.c_int32)),
+        ("rt_consts", C.POINTER(C.c_float)), ("rt_lengths", C.POINTER(C.c_int32)),
+        ("sigma_dtype", C.c_int32),
+    ]
+
+
+class Info(C.Structure):
+    _fields_ = [
+        ("struct_size", C.c_uint32), ("state", C.c_int32), ("n_features", C.c_int32),
+        ("n_train", C.c_int64), ("n_test", C.c_int64), ("n_cases", C.c_int64),
+        ("n_cases_padded", C.c_int64), ("pop_size", C.c_int32), ("n_random_trees", C.c_int32),
+        ("pop_max_genes", C.c_int32), ("rt_max_genes", C.c_int32), ("generation", C.c_int32),
+        ("evolve_tile_cases", C.c_int32), ("evolve_offspring_per_cta", C.c_int32),
+        ("kernel_launches", C.c_int64), ("device_bytes", C.c_int64),
+    ]
+
+
+P = C.c_void_p
+_SIGS = {
+    "gsgp_config_default": (None, [C.POINTER(Config)]),
+    "gsgp_config_error": (C.c_char_p, [C.POINTER(Config)]),
+    "gsgp_create": (C.c_int, [C.POINTER(Config), C.POINTER(P)]),
+    "gsgp_load": (C.c_int, [P, P, P, C.c_int64, C.c_int32, P, P, C.c_int64]),
+    "gsgp_load_device": (C.c_int, [P, P, P, C.c_int64, C.c_int32, P, P, C.c_int64]),
+    "gsgp_init": (C.c_int, [P]),
+    "gsgp_evolve": (C.c_int, [P, C.c_int32, P, P]),
+    "gsgp_best_trace": (C.c_int, [P, C.POINTER(Trace)]),
+    "gsgp_predict": (C.c_int, [P, P, C.c_int64, P]),
+    "gsgp_predict_device": (C.c_int, [P, P, C.c_int64, P]),
+    "gsgp_last_error": (C.c_char_p, [P]),
+    "gsgp_destroy": (None, [P]),
+    "gsgp_get_info": (C.c_int, [P, C.POINTER(Info)]),
+    "gsgp_get_programs": (C.c_int, [P, C.c_int32, P, P, P]),
+    "gsgp_get_semantics": (C.c_int, [P, C.c_int32, C.c_int32, C.c_int32, P]),
+    "gsgp_get_fitness": (C.c_int, [P, P, P]),
+    "gsgp_get_trace": (C.c_int, [P, C.c_int32, C.c_int32, P, P, P, P]),
+    "gsgp_set_kernel_timing": (C.c_int, [P, C.c_int32]),
+    "gsgp_kernel_times": (C.c_int, [P, P, C.c_int32, P]),
+    "gsgp_rng_words": (C.c_int, [C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint32, C.c_int32, P, P]),
+}
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libgsgp.so (raises when it has not been built: there is no
+    fallback implementation)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"libgsgp.so is not built ({path}); run "
+                          "`python -c 'import __graft_entry__ as g; g.build()'`")
+    lib = C.CDLL(path)
+    for name, (res, args) in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def exported_names():
+    return list(_SIGS)
+
+
+def _ptr(a) -> Optional[int]:
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        assert a.flags["C_CONTIGUOUS"]
+        return a.ctypes.data
+    if hasattr(a, "data_ptr"):        # torch tensor
+        assert a.is_contiguous()
+        return a.data_ptr()
+    return int(a)
+
+
+def default_config(**kw) -> Config:
+    lib = load_library()
+    cfg = Config()
+    lib.gsgp_config_default(C.byref(cfg))
+    for k, v in kw.items():
+        if not hasattr(cfg, k):
+            raise TypeError(f"unknown config field {k}")
+        setattr(cfg, k, v)
+    return cfg
+
+
+class TorchAllocator:
+    """Device allocator hooks backed by torch's caching allocator."""
+
+    def __init__(self, device: int = 0):
+        import torch
+        self.torch = torch
+        self.device = device
+
+        def _alloc(user, nbytes, stream):
+            try:
+                return int(torch.cuda.caching_allocator_alloc(int(nbytes), self.device,
+                                                              stream if stream else 0))
+            except Exception:
+                return None
+
+        def _free(user, ptr, stream):
+            if ptr:
+                torch.cuda.caching_allocator_delete(ptr)
+
+        self.alloc_fn = ALLOC_FN(_alloc)
+        self.free_fn = FREE_FN(_free)
+
+
+class Run:
+    """One GSGP run (one gsgp_ctx)."""
+
+    def __init__(self, cfg: Optional[Config] = None, stream=None, torch_allocator=False, **kw):
+        self.lib = load_library()
+        self.cfg = cfg if cfg is not None else default_config(**kw)
+        if stream is not None:
+            self.cfg.stream = stream if isinstance(stream, int) else stream.cuda_stream
+        self._allocator = None
+        if torch_allocator:
+            self._allocator = TorchAllocator()
+            self.cfg.alloc = self._allocator.alloc_fn
+            self.cfg.free = self._allocator.free_fn
+        self.ctx = P()
+        st = self.lib.gsgp_create(C.byref(self.cfg), C.byref(self.ctx))
+        if st != OK:
+            raise GsgpError(st, self.lib.gsgp_config_error(C.byref(self.cfg)).decode())
+
+    def _check(self, st):
+        if st != OK:
+            raise GsgpError(st, self.lib.gsgp_last_error(self.ctx).decode())
+
+    def close(self):
+        if self.ctx:
+            self.lib.gsgp_destroy(self.ctx)
+            self.ctx = P()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # -- data -------------------------------------------------------------
+    def load(self, X_train, y_train, X_test=None, y_test=None):
+        X_train = np.ascontiguousarray(X_train, dtype=np.float32)
+        y_train = np.ascontiguousarray(y_train, dtype=np.float32)
+        n_te = 0 if X_test is None else len(X_test)
+        if n_te:
+            X_test = np.ascontiguousarray(X_test, dtype=np.float32)
+            y_test = np.ascontiguousarray(y_test, dtype=np.float32)
+        self._check(self.lib.gsgp_load(self.ctx, _ptr(X_train), _ptr(y_train), len(X_train),
+                                       X_train.shape[1] if X_train.ndim == 2 else 0,
+                                       _ptr(X_test) if n_te else None,
+                                       _ptr(y_test) if n_te else None, n_te))
+
+    def load_device(self, X_train, y_train, X_test=None, y_test=None):
+        """torch CUDA float32 tensors, row-major (cases x features)."""
+        n_te = 0 if X_test is None else int(X_test.shape[0])
+        self._check(self.lib.gsgp_load_device(
+            self.ctx, _ptr(X_train), _ptr(y_train), int(X_train.shape[0]), int(X_train.shape[1]),
+            _ptr(X_test) if n_te else None, _ptr(y_test) if n_te else None, n_te))
+
+    def init(self):
+        self._check(self.lib.gsgp_init(self.ctx))
+
+    def evolve(self, generations: int, log: bool = True):
+        if not log:
+            self._check(self.lib.gsgp_evolve(self.ctx, generations, None, None))
+            return None
+        tr = np.zeros(generations, dtype=np.float64)
+        te = np.zeros(generations, dtype=np.float64)
+        self._check(self.lib.gsgp_evolve(self.ctx, generations, _ptr(tr), _ptr(te)))
+        return tr, te
+
+    # -- best individual ---------------------------------------------------
+    def best_trace(self) -> dict:
+        t = Trace()
+        t.struct_size = C.sizeof(Trace)
+        self._check(self.lib.gsgp_best_trace(self.ctx, C.byref(t)))
+        G, r, K, Kr = t.n_generations, t.n_random_trees, t.max_genes, t.rt_max_genes
+        out = {
+            "anc_genes": np.zeros(K, np.int32), "anc_consts": np.zeros(K, np.float32),
+            "parent": np.zeros(max(G, 1), np.int32), "rt1": np.zeros(max(G, 1), np.int32),
+            "rt2": np.zeros(max(G, 1), np.int32), "ms": np.zeros(max(G, 1), np.float32),
+            "coef": np.zeros(r, np.float64), "rt_genes": np.zeros((r, Kr), np.int32),
+            "rt_consts": np.zeros((r, Kr), np.float32), "rt_lengths": np.zeros(r, np.int32),
+        }
+
+        def p(a, ct):
+            return a.ctypes.data_as(C.POINTER(ct))
+
+        t.ancestor_genes = p(out["anc_genes"], C.c_int32)
+        t.ancestor_consts = p(out["anc_consts"], C.c_float)
+        t.lineage_parent = p(out["parent"], C.c_int32)
+        t.lineage_rt1 = p(out["rt1"], C.c_int32)
+        t.lineage_rt2 = p(out["rt2"], C.c_int32)
+        t.lineage_ms = p(out["ms"], C.c_float)
+        t.coef = p(out["coef"], C.c_double)
+        t.rt_genes = p(out["rt_genes"], C.c_int32)
+        t.rt_consts = p(out["rt_consts"], C.c_float)
+        t.rt_lengths = p(out["rt_lengths"], C.c_int32)
+        self._check(self.lib.gsgp_best_trace(self.ctx, C.byref(t)))
+        for k in ("parent", "rt1", "rt2", "ms"):
+            out[k] = out[k][:G]
+        out.update(best_slot=t.best_slot, best_train_rmse=t.best_train_rmse,
+                   best_test_rmse=t.best_test_rmse, ancestor=t.ancestor,
+                   ancestor_length=t.ancestor_length, n_generations=G,
+                   sigma_dtype=t.sigma_dtype)
+        return out
+
+    def predict(self, X) -> np.ndarray:
+        X = np.ascontiguousarray(X, dtype=np.float32)
+        y = np.zeros(len(X), dtype=np.float64)
+        self._check(self.lib.gsgp_predict(self.ctx, _ptr(X), len(X), _ptr(y)))
+        return y
+
+    def predict_device(self, X, y):
+        self._check(self.lib.gsgp_predict_device(self.ctx, _ptr(X), int(X.shape[0]), _ptr(y)))
+
+    # -- introspection -----------------------------------------------------
+    def info(self) -> Info:
+        i = Info()
+        i.struct_size = C.sizeof(Info)
+        self._check(self.lib.gsgp_get_info(self.ctx, C.byref(i)))
+        return i
+
+    def programs(self, pool: int):
+        i = self.info()
+        cnt = i.pop_size if pool == POOL_POPULATION else i.n_random_trees
+        K = i.pop_max_genes if pool == POOL_POPULATION else i.rt_max_genes
+        g = np.zeros((cnt, K), np.int32)
+        c = np.zeros((cnt, K), np.float32)
+        L = np.zeros(cnt, np.int32)
+        self._check(self.lib.gsgp_get_programs(self.ctx, pool, _ptr(g), _ptr(c), _ptr(L)))
+        return g, c, L
+
+    def semantics(self, pool: int, row0: int = 0, rows: Optional[int] = None) -> np.ndarray:
+        i = self.info()
+        cnt = i.pop_size if pool == POOL_POPULATION else i.n_random_trees
+        rows = cnt - row0 if rows is None else rows
+        out = np.zeros((rows, i.n_cases), np.float32)
+        self._check(self.lib.gsgp_get_semantics(self.ctx, pool, row0, rows, _ptr(out)))
+        return out
+
+    def fitness(self):
+        m = self.info().pop_size
+        tr = np.zeros(m, np.float64)
+        te = np.zeros(m, np.float64)
+        self._check(self.lib.gsgp_get_fitness(self.ctx, _ptr(tr), _ptr(te)))
+        return tr, te
+
+    def trace(self, g0: int = 0, count: Optional[int] = None):
+        i = self.info()
+        count = i.generation - g0 if count is None else count
+        m = i.pop_size
+        a = [np.zeros((count, m), np.int32) for _ in range(3)]
+        ms = np.zeros((count, m), np.float32)
+        self._check(self.lib.gsgp_get_trace(self.ctx, g0, count, _ptr(a[0]), _ptr(a[1]),
+                                            _ptr(a[2]), _ptr(ms)))
+        return a[0], a[1], a[2], ms
+
+    def set_kernel_timing(self, enabled: bool):
+        self._check(self.lib.gsgp_set_kernel_timing(self.ctx, int(enabled)))
+
+    def kernel_times(self, cap: int = 1 << 16) -> np.ndarray:
+        out = np.zeros(cap, np.float32)
+        n = C.c_int32(0)
+        self._check(self.lib.gsgp_kernel_times(self.ctx, _ptr(out), cap, C.byref(n)))
+        return out[:n.value].copy()
+
+
+def rng_words(seed: int, run: int, gen_or_purpose: int, individual: int, n_words: int,
+              stream=None) -> np.ndarray:
+    lib = load_library()
+    out = np.zeros(n_words, np.uint32)
+    st = lib.gsgp_rng_words(seed, run, gen_or_purpose, individual, n_words, _ptr(out),
+                            stream.cuda_stream if stream is not None and not isinstance(stream, int)
+                            else stream)
+    if st != OK:
+        raise GsgpError(st, "gsgp_rng_words failed")
+    return out

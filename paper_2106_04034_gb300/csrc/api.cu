@@ -1,0 +1,1002 @@
+// C ABI of the GSGP library: context, state machine, device memory, stream
+// ordering, CUDA-graph replay of the generation loop and host-side model
+// reconstruction.  Every step of the method runs in the kernels of
+// k_init.cu, k_generation.cu and k_predict.cu.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "gsgp.h"
+#include "kernels.cuh"
+
+using namespace gsgp;
+
+struct gsgp_ctx {
+  gsgp_config cfg{};
+  std::string err;
+  int state = 0;   // 0 created, 1 loaded, 2 initialised
+  int device = -1;
+  cudaStream_t stream = nullptr;
+  cudaStream_t cap_stream = nullptr;
+
+  // fitness cases
+  int l = 0;
+  int64_t n_tr = 0, n_te = 0, N = 0, n_pad = 0;
+  float *X = nullptr;   // [l][n_pad]
+  float *t = nullptr;   // [n_pad]
+
+  // run state
+  int Kp = 0, Kr = 0;
+  int tiles_interp = 0, tiles_gen = 0;
+  GenShape shape{2, 4};
+  int64_t layout_key[7] = {0, 0, 0, 0, 0, 0, 0};
+  int *P_genes = nullptr, *P_len = nullptr, *R_genes = nullptr, *R_len = nullptr;
+  float *P_consts = nullptr, *R_consts = nullptr;
+  float *pool = nullptr;
+  void *sigR = nullptr;
+  int *perm = nullptr;
+  double *fit = nullptr, *fit_te = nullptr;
+  double2 *partial = nullptr;
+  unsigned *tile_count = nullptr;
+  DevState *dstate = nullptr;
+  int4 *trace = nullptr;
+  double2 *best_log = nullptr;
+  int gcap = 0;
+  int4 *lineage = nullptr;
+  int lineage_cap = 0;
+  int *d_anc = nullptr;
+  unsigned *d_flag = nullptr;
+  int gen = 0;
+
+  // CUDA graph of `graph_u` generations, replayed by gsgp_evolve
+  cudaGraphExec_t gexec = nullptr;
+  int graph_u = 0;
+  bool graph_dirty = true;
+
+  // generation-kernel timing
+  bool timing = false;
+  std::vector<cudaEvent_t> ev0, ev1;
+  int ev_used = 0;
+
+  // rebuilt best model (valid while model_gen == gen)
+  int model_gen = -1;
+  int best_slot = 0, ancestor = 0;
+  double best_tr = 0.0, best_te = 0.0;
+  std::vector<int4> h_lineage;
+  std::vector<double> coef;
+  int *d_terms = nullptr;
+  double *d_coef = nullptr;
+  int terms_cap = 0;
+  int n_terms = 0;
+
+  int64_t launches = 0;
+  int64_t dev_bytes = 0;
+  std::unordered_map<void *, size_t> allocs;
+};
+
+// ---------------------------------------------------------------- errors --
+static gsgp_status fail(gsgp_ctx *c, gsgp_status st, const char *fmt, ...) {
+  if (c) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    c->err = buf;
+  }
+  return st;
+}
+
+static gsgp_status cuda_fail(gsgp_ctx *c, cudaError_t e, const char *what, int line) {
+  cudaGetLastError();
+  return fail(c, e == cudaErrorMemoryAllocation ? GSGP_E_OOM : GSGP_E_CUDA, "%s (api.cu:%d): %s",
+              what, line, cudaGetErrorString(e));
+}
+
+#define CK(call)                                                      \
+  do {                                                                \
+    cudaError_t e_ = (call);                                          \
+    if (e_ != cudaSuccess) return cuda_fail(c, e_, #call, __LINE__);  \
+  } while (0)
+
+#define LAUNCH(n, call)      \
+  do {                       \
+    CK(call);                \
+    c->launches += (n);      \
+  } while (0)
+
+#define TRY(expr)                                  \
+  do {                                             \
+    gsgp_status s_ = (expr);                       \
+    if (s_ != GSGP_OK) return s_;                  \
+  } while (0)
+
+#define API_GUARD(c)                                                                   \
+  if (!(c)) return GSGP_E_INVALID;                                                     \
+  (c)->err.clear();                                                                    \
+  try {
+#define API_END(c)                                                                     \
+  }                                                                                    \
+  catch (const std::bad_alloc &) {                                                     \
+    return fail((c), GSGP_E_OOM, "host allocation failed");                            \
+  }                                                                                    \
+  catch (...) {                                                                        \
+    return fail((c), GSGP_E_INVALID, "unexpected host exception");                     \
+  }
+
+// ---------------------------------------------------------------- memory --
+static gsgp_status dalloc(gsgp_ctx *c, void **p, size_t bytes) {
+  *p = nullptr;
+  if (bytes == 0) bytes = 16;
+  if (c->cfg.alloc) {
+    *p = c->cfg.alloc(c->cfg.alloc_user, bytes, c->stream);
+    if (!*p) return fail(c, GSGP_E_OOM, "device allocator returned NULL for %zu bytes", bytes);
+  } else {
+    cudaError_t e = cudaMallocAsync(p, bytes, c->stream);
+    if (e != cudaSuccess) {
+      *p = nullptr;
+      cudaGetLastError();
+      return fail(c, e == cudaErrorMemoryAllocation ? GSGP_E_OOM : GSGP_E_CUDA,
+                  "device allocation of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
+    }
+  }
+  c->allocs[*p] = bytes;
+  c->dev_bytes += (int64_t)bytes;
+  return GSGP_OK;
+}
+
+template <typename T>
+static gsgp_status dalloc_n(gsgp_ctx *c, T **p, size_t count) {
+  void *v = nullptr;
+  gsgp_status s = dalloc(c, &v, count * sizeof(T));
+  *p = static_cast<T *>(v);
+  return s;
+}
+
+template <typename T>
+static void dfree(gsgp_ctx *c, T *&p) {
+  if (!p) return;
+  void *v = (void *)p;
+  auto it = c->allocs.find(v);
+  if (it != c->allocs.end()) {
+    c->dev_bytes -= (int64_t)it->second;
+    c->allocs.erase(it);
+  }
+  if (c->cfg.alloc)
+    c->cfg.free(c->cfg.alloc_user, v, c->stream);
+  else
+    cudaFreeAsync(v, c->stream);
+  p = nullptr;
+}
+
+static void free_run_buffers(gsgp_ctx *c) {
+  dfree(c, c->P_genes);
+  dfree(c, c->P_consts);
+  dfree(c, c->P_len);
+  dfree(c, c->R_genes);
+  dfree(c, c->R_consts);
+  dfree(c, c->R_len);
+  dfree(c, c->pool);
+  dfree(c, c->sigR);
+  dfree(c, c->perm);
+  dfree(c, c->fit);
+  dfree(c, c->fit_te);
+  dfree(c, c->partial);
+  dfree(c, c->tile_count);
+  dfree(c, c->dstate);
+  dfree(c, c->trace);
+  dfree(c, c->best_log);
+  dfree(c, c->lineage);
+  dfree(c, c->d_anc);
+  dfree(c, c->d_terms);
+  dfree(c, c->d_coef);
+  c->gcap = 0;
+  c->lineage_cap = 0;
+  c->terms_cap = 0;
+  memset(c->layout_key, 0, sizeof c->layout_key);
+  c->graph_dirty = true;
+}
+
+static void free_graph(gsgp_ctx *c) {
+  if (c->gexec) cudaGraphExecDestroy(c->gexec);
+  c->gexec = nullptr;
+  c->graph_u = 0;
+}
+
+// ---------------------------------------------------------------- config --
+extern "C" void gsgp_config_default(gsgp_config *cfg) {
+  if (!cfg) return;
+  memset(cfg, 0, sizeof *cfg);
+  cfg->struct_size = sizeof(gsgp_config);
+  cfg->seed = 1;
+  cfg->run = 0;
+  cfg->pop_size = 1024;
+  cfg->n_random_trees = 1024;
+  cfg->pop_min_depth = 2;
+  cfg->pop_max_depth = 6;
+  cfg->rt_min_depth = 2;
+  cfg->rt_max_depth = 6;
+  cfg->const_lo = -1.0f;
+  cfg->const_hi = 1.0f;
+  cfg->p_grow_function = 0.5f;
+  cfg->p_feature_given_terminal = (float)(0.14 / 0.18);   /* 7/9 rounded once */
+  cfg->protect_eps = 1e-3f;
+  cfg->ms = 0.1f;
+  cfg->ms_mode = 0;
+  cfg->tournament_size = 4;
+  cfg->elitism = 1;
+  cfg->sigma_dtype = GSGP_SIGMA_F32;
+}
+
+static bool prob_ok(float p) { return std::isfinite(p) && p >= 0.0f && p <= 1.0f; }
+
+static const char *check_config(const gsgp_config *cfg) {
+  if (cfg->struct_size != sizeof(gsgp_config)) return "struct_size does not match this library";
+  if (cfg->pop_size < 2 || cfg->pop_size > 65536) return "pop_size must be in [2, 65536]";
+  if (cfg->n_random_trees < 1 || cfg->n_random_trees > 65536)
+    return "n_random_trees must be in [1, 65536]";
+  if (cfg->pop_min_depth < 0 || cfg->pop_max_depth > kMaxDepth ||
+      cfg->pop_min_depth > cfg->pop_max_depth)
+    return "population depths must satisfy 0 <= min <= max <= 10";
+  if (cfg->rt_min_depth < 0 || cfg->rt_max_depth > kMaxDepth ||
+      cfg->rt_min_depth > cfg->rt_max_depth)
+    return "random-tree depths must satisfy 0 <= min <= max <= 10";
+  if (!std::isfinite(cfg->const_lo) || !std::isfinite(cfg->const_hi) ||
+      cfg->const_lo > cfg->const_hi)
+    return "constant range must be finite with lo <= hi";
+  if (!prob_ok(cfg->p_grow_function) || !prob_ok(cfg->p_feature_given_terminal))
+    return "probabilities must be in [0, 1]";
+  if (!std::isfinite(cfg->protect_eps) || cfg->protect_eps < 0.0f)
+    return "protect_eps must be finite and >= 0";
+  if (!std::isfinite(cfg->ms)) return "ms must be finite";
+  if (cfg->ms_mode != 0 && cfg->ms_mode != 1) return "ms_mode must be 0 or 1";
+  if (cfg->tournament_size < 0 || cfg->tournament_size > 64)
+    return "tournament_size must be in [0, 64]";
+  if (cfg->elitism != 0 && cfg->elitism != 1) return "elitism must be 0 or 1";
+  if (cfg->sigma_dtype != GSGP_SIGMA_F32 && cfg->sigma_dtype != GSGP_SIGMA_BF16)
+    return "sigma_dtype must be GSGP_SIGMA_F32 or GSGP_SIGMA_BF16";
+  if ((cfg->alloc == nullptr) != (cfg->free == nullptr))
+    return "alloc and free must be given together";
+  return nullptr;
+}
+
+extern "C" gsgp_status gsgp_create(const gsgp_config *cfg, gsgp_ctx **out) {
+  if (!out) return GSGP_E_INVALID;
+  *out = nullptr;
+  if (!cfg) return GSGP_E_INVALID;
+  if (check_config(cfg)) return GSGP_E_INVALID;
+  gsgp_ctx *c = new (std::nothrow) gsgp_ctx();
+  if (!c) return GSGP_E_OOM;
+  c->cfg = *cfg;
+  c->stream = static_cast<cudaStream_t>(cfg->stream);
+  *out = c;
+  return GSGP_OK;
+}
+
+// Same check with a message for the caller that kept a context.
+extern "C" const char *gsgp_config_error(const gsgp_config *cfg) {
+  if (!cfg) return "NULL config";
+  const char *e = check_config(cfg);
+  return e ? e : "";
+}
+
+extern "C" const char *gsgp_last_error(const gsgp_ctx *c) { return c ? c->err.c_str() : ""; }
+
+static gsgp_status use_device(gsgp_ctx *c) {
+  if (c->device < 0) CK(cudaGetDevice(&c->device));
+  CK(cudaSetDevice(c->device));
+  return GSGP_OK;
+}
+
+// ------------------------------------------------------------------ load --
+static bool host_finite(const float *v, int64_t n) {
+  for (int64_t i = 0; i < n; ++i)
+    if (!std::isfinite(v[i])) return false;
+  return true;
+}
+
+static gsgp_status check_shapes(gsgp_ctx *c, const float *Xtr, const float *ytr, int64_t ntr,
+                                int32_t l, const float *Xte, const float *yte, int64_t nte) {
+  if (ntr < 1) return fail(c, GSGP_E_INVALID, "n_train must be >= 1");
+  if (nte < 0) return fail(c, GSGP_E_INVALID, "n_test must be >= 0");
+  if (l < 1 || l > 65535) return fail(c, GSGP_E_INVALID, "n_features must be in [1, 65535]");
+  if (!Xtr || !ytr) return fail(c, GSGP_E_INVALID, "training data pointers must not be NULL");
+  if (nte > 0 && (!Xte || !yte)) return fail(c, GSGP_E_INVALID, "test data pointers are NULL");
+  if (ntr + nte > (int64_t)0x7fffff00) return fail(c, GSGP_E_INVALID, "too many fitness cases");
+  return GSGP_OK;
+}
+
+static gsgp_status prepare_data(gsgp_ctx *c, int64_t ntr, int32_t l, int64_t nte) {
+  TRY(use_device(c));
+  const int64_t N = ntr + nte;
+  const int64_t n_pad = (N + 63) / 64 * 64;
+  if (c->X && (c->l != l || c->n_pad != n_pad)) {
+    dfree(c, c->X);
+    dfree(c, c->t);
+  }
+  if (c->n_pad != n_pad) free_run_buffers(c);
+  c->l = l;
+  c->n_tr = ntr;
+  c->n_te = nte;
+  c->N = N;
+  c->n_pad = n_pad;
+  if (!c->X) TRY(dalloc_n(c, &c->X, (size_t)l * n_pad));
+  if (!c->t) TRY(dalloc_n(c, &c->t, (size_t)n_pad));
+  CK(cudaMemsetAsync(c->X, 0, sizeof(float) * (size_t)l * n_pad, c->stream));
+  CK(cudaMemsetAsync(c->t, 0, sizeof(float) * (size_t)n_pad, c->stream));
+  c->state = 1;
+  c->model_gen = -1;
+  return GSGP_OK;
+}
+
+extern "C" gsgp_status gsgp_load(gsgp_ctx *c, const float *Xtr, const float *ytr, int64_t ntr,
+                                 int32_t l, const float *Xte, const float *yte, int64_t nte) {
+  API_GUARD(c)
+  TRY(check_shapes(c, Xtr, ytr, ntr, l, Xte, yte, nte));
+  if (!host_finite(Xtr, ntr * l) || !host_finite(ytr, ntr) ||
+      (nte > 0 && (!host_finite(Xte, nte * l) || !host_finite(yte, nte))))
+    return fail(c, GSGP_E_INVALID, "non-finite value in the fitness cases");
+  TRY(prepare_data(c, ntr, l, nte));
+  float *stage = nullptr;
+  const int64_t rows = ntr > nte ? ntr : nte;
+  TRY(dalloc_n(c, &stage, (size_t)rows * l));
+  CK(cudaMemcpyAsync(stage, Xtr, sizeof(float) * (size_t)ntr * l, cudaMemcpyHostToDevice,
+                     c->stream));
+  LAUNCH(1, launch_transpose(stage, ntr, l, c->X, c->n_pad, 0, c->stream));
+  CK(cudaMemcpyAsync(c->t, ytr, sizeof(float) * (size_t)ntr, cudaMemcpyHostToDevice, c->stream));
+  if (nte > 0) {
+    CK(cudaMemcpyAsync(stage, Xte, sizeof(float) * (size_t)nte * l, cudaMemcpyHostToDevice,
+                       c->stream));
+    LAUNCH(1, launch_transpose(stage, nte, l, c->X, c->n_pad, ntr, c->stream));
+    CK(cudaMemcpyAsync(c->t + ntr, yte, sizeof(float) * (size_t)nte, cudaMemcpyHostToDevice,
+                       c->stream));
+  }
+  dfree(c, stage);
+  return GSGP_OK;
+  API_END(c)
+}
+
+extern "C" gsgp_status gsgp_load_device(gsgp_ctx *c, const float *Xtr, const float *ytr,
+                                        int64_t ntr, int32_t l, const float *Xte,
+                                        const float *yte, int64_t nte) {
+  API_GUARD(c)
+  TRY(check_shapes(c, Xtr, ytr, ntr, l, Xte, yte, nte));
+  TRY(use_device(c));
+  if (!c->d_flag) TRY(dalloc_n(c, &c->d_flag, 1));
+  CK(cudaMemsetAsync(c->d_flag, 0, sizeof(unsigned), c->stream));
+  LAUNCH(1, launch_nonfinite_check(Xtr, ntr * l, c->d_flag, c->stream));
+  LAUNCH(1, launch_nonfinite_check(ytr, ntr, c->d_flag, c->stream));
+  if (nte > 0) {
+    LAUNCH(1, launch_nonfinite_check(Xte, nte * l, c->d_flag, c->stream));
+    LAUNCH(1, launch_nonfinite_check(yte, nte, c->d_flag, c->stream));
+  }
+  unsigned bad = 0;
+  CK(cudaMemcpyAsync(&bad, c->d_flag, sizeof bad, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  if (bad) return fail(c, GSGP_E_INVALID, "non-finite value in the fitness cases");
+  TRY(prepare_data(c, ntr, l, nte));
+  LAUNCH(1, launch_transpose(Xtr, ntr, l, c->X, c->n_pad, 0, c->stream));
+  CK(cudaMemcpyAsync(c->t, ytr, sizeof(float) * (size_t)ntr, cudaMemcpyDeviceToDevice, c->stream));
+  if (nte > 0) {
+    LAUNCH(1, launch_transpose(Xte, nte, l, c->X, c->n_pad, ntr, c->stream));
+    CK(cudaMemcpyAsync(c->t + ntr, yte, sizeof(float) * (size_t)nte, cudaMemcpyDeviceToDevice,
+                       c->stream));
+  }
+  return GSGP_OK;
+  API_END(c)
+}
+
+// ------------------------------------------------------------------ init --
+static GenParams gen_params(gsgp_ctx *c) {
+  GenParams p{};
+  p.target = c->t;
+  p.pool = c->pool;
+  p.sigma_r = c->sigR;
+  p.perm = c->perm;
+  p.fit = c->fit;
+  p.fit_te = c->fit_te;
+  p.partial = c->partial;
+  p.tile_count = c->tile_count;
+  p.trace = c->trace;
+  p.best_log = c->best_log;
+  p.state = c->dstate;
+  p.n_pad = c->n_pad;
+  p.m = c->cfg.pop_size;
+  p.r = c->cfg.n_random_trees;
+  p.tsize = c->cfg.tournament_size;
+  p.n_train = (int)c->n_tr;
+  p.n_cases = (int)c->N;
+  p.tiles = c->tiles_gen;
+  p.ms_mode = c->cfg.ms_mode;
+  p.ms = c->cfg.ms;
+  p.key = make_uint2((uint32_t)(c->cfg.seed & 0xffffffffu), (uint32_t)(c->cfg.seed >> 32));
+  p.run = c->cfg.run;
+  p.elitism = c->cfg.elitism;
+  return p;
+}
+
+static gsgp_status ensure_trace(gsgp_ctx *c, int need) {
+  if (need <= c->gcap) return GSGP_OK;
+  const int m = c->cfg.pop_size;
+  int cap = c->gcap ? c->gcap : 64;
+  while (cap < need) cap *= 2;
+  int4 *tr = nullptr;
+  double2 *bl = nullptr;
+  TRY(dalloc_n(c, &tr, (size_t)cap * m));
+  TRY(dalloc_n(c, &bl, (size_t)cap));
+  if (c->gen > 0 && c->trace) {
+    CK(cudaMemcpyAsync(tr, c->trace, sizeof(int4) * (size_t)c->gen * m, cudaMemcpyDeviceToDevice,
+                       c->stream));
+    CK(cudaMemcpyAsync(bl, c->best_log, sizeof(double2) * (size_t)c->gen,
+                       cudaMemcpyDeviceToDevice, c->stream));
+  }
+  dfree(c, c->trace);
+  dfree(c, c->best_log);
+  c->trace = tr;
+  c->best_log = bl;
+  c->gcap = cap;
+  c->graph_dirty = true;
+  return GSGP_OK;
+}
+
+extern "C" gsgp_status gsgp_init(gsgp_ctx *c) {
+  API_GUARD(c)
+  if (c->state < 1) return fail(c, GSGP_E_STATE, "gsgp_init before gsgp_load");
+  TRY(use_device(c));
+  const gsgp_config &cf = c->cfg;
+  const int m = cf.pop_size, r = cf.n_random_trees;
+  const int Kp = (1 << (cf.pop_max_depth + 1)) - 1;
+  const int Kr = (1 << (cf.rt_max_depth + 1)) - 1;
+  const int W = gen_tile_cases(c->shape);
+  const int64_t key[7] = {m, r, c->n_pad, Kp, Kr, cf.sigma_dtype, W};
+  if (memcmp(key, c->layout_key, sizeof key) != 0) {
+    free_run_buffers(c);
+    c->Kp = Kp;
+    c->Kr = Kr;
+    c->tiles_interp = (int)((c->n_pad + 1023) / 1024);
+    c->tiles_gen = (int)((c->n_pad + W - 1) / W);
+    const int tiles_max = c->tiles_interp > c->tiles_gen ? c->tiles_interp : c->tiles_gen;
+    TRY(dalloc_n(c, &c->P_genes, (size_t)m * Kp));
+    TRY(dalloc_n(c, &c->P_consts, (size_t)m * Kp));
+    TRY(dalloc_n(c, &c->P_len, (size_t)m));
+    TRY(dalloc_n(c, &c->R_genes, (size_t)r * Kr));
+    TRY(dalloc_n(c, &c->R_consts, (size_t)r * Kr));
+    TRY(dalloc_n(c, &c->R_len, (size_t)r));
+    TRY(dalloc_n(c, &c->pool, (size_t)2 * m * c->n_pad));
+    const size_t sbytes = cf.sigma_dtype == GSGP_SIGMA_BF16 ? 2 : 4;
+    TRY(dalloc(c, &c->sigR, sbytes * (size_t)r * c->n_pad));
+    TRY(dalloc_n(c, &c->perm, (size_t)4 * m));
+    TRY(dalloc_n(c, &c->fit, (size_t)2 * m));
+    TRY(dalloc_n(c, &c->fit_te, (size_t)2 * m));
+    TRY(dalloc_n(c, &c->partial, (size_t)m * tiles_max));
+    TRY(dalloc_n(c, &c->tile_count, (size_t)m));
+    TRY(dalloc_n(c, &c->dstate, 1));
+    TRY(dalloc_n(c, &c->d_anc, 1));
+    memcpy(c->layout_key, key, sizeof key);
+    c->graph_dirty = true;
+  }
+  c->gen = 0;
+  c->model_gen = -1;
+  TRY(ensure_trace(c, 64));
+  const uint2 k2 = make_uint2((uint32_t)(cf.seed & 0xffffffffu), (uint32_t)(cf.seed >> 32));
+  LAUNCH(1, launch_treegen(m, cf.pop_min_depth, cf.pop_max_depth, Kp, c->l, k2, cf.run,
+                           kPurposePop, cf.p_grow_function, cf.p_feature_given_terminal,
+                           cf.const_lo, cf.const_hi, c->P_genes, c->P_consts, c->P_len,
+                           c->stream));
+  LAUNCH(1, launch_treegen(r, cf.rt_min_depth, cf.rt_max_depth, Kr, c->l, k2, cf.run,
+                           kPurposeRt, cf.p_grow_function, cf.p_feature_given_terminal,
+                           cf.const_lo, cf.const_hi, c->R_genes, c->R_consts, c->R_len,
+                           c->stream));
+  InterpParams ip{};
+  ip.X = c->X;
+  ip.target = c->t;
+  ip.n_pad = c->n_pad;
+  ip.n_train = (int)c->n_tr;
+  ip.n_cases = (int)c->N;
+  ip.tiles = c->tiles_interp;
+  ip.protect_eps = cf.protect_eps;
+  // population semantics + squared errors (rows 0..m-1 of the pool)
+  ip.genes = c->P_genes;
+  ip.consts = c->P_consts;
+  ip.lengths = c->P_len;
+  ip.K = Kp;
+  ip.stack_slots = cf.pop_max_depth + 1;
+  ip.out = c->pool;
+  ip.partial = c->partial;
+  LAUNCH(1, launch_interpret(0, ip, m, c->stream));
+  // random-tree semantics wrapped by the logistic function
+  ip.genes = c->R_genes;
+  ip.consts = c->R_consts;
+  ip.lengths = c->R_len;
+  ip.K = Kr;
+  ip.stack_slots = cf.rt_max_depth + 1;
+  ip.out = c->sigR;
+  ip.partial = nullptr;
+  LAUNCH(1, launch_interpret(cf.sigma_dtype == GSGP_SIGMA_BF16 ? 2 : 1, ip, r, c->stream));
+  LAUNCH(1, launch_fitness_finalize(c->partial, c->tiles_interp, m, (int)c->n_tr, (int)c->n_te,
+                                    c->fit, c->fit_te, c->stream));
+  LAUNCH(1, launch_init_state(m, c->perm, c->tile_count, c->fit, c->dstate, c->stream));
+  c->state = 2;
+  return GSGP_OK;
+  API_END(c)
+}
+
+// ---------------------------------------------------------------- evolve --
+static gsgp_status build_graph(gsgp_ctx *c, int u) {
+  free_graph(c);
+  if (!c->cap_stream) CK(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+  const GenParams p = gen_params(c);
+  CK(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+  cudaError_t le = cudaSuccess;
+  for (int k = 0; k < u && le == cudaSuccess; ++k)
+    le = launch_generation(p, c->cfg.sigma_dtype == GSGP_SIGMA_BF16, c->shape, c->cap_stream);
+  cudaGraph_t graph = nullptr;
+  cudaError_t ee = cudaStreamEndCapture(c->cap_stream, &graph);
+  if (le != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    return cuda_fail(c, le, "launch_generation (capture)", __LINE__);
+  }
+  if (ee != cudaSuccess) return cuda_fail(c, ee, "cudaStreamEndCapture", __LINE__);
+  cudaError_t ie = cudaGraphInstantiate(&c->gexec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (ie != cudaSuccess) {
+    c->gexec = nullptr;
+    return cuda_fail(c, ie, "cudaGraphInstantiate", __LINE__);
+  }
+  c->graph_u = u;
+  c->graph_dirty = false;
+  return GSGP_OK;
+}
+
+static gsgp_status ensure_events(gsgp_ctx *c, int need) {
+  while ((int)c->ev0.size() < need) {
+    cudaEvent_t a, b;
+    CK(cudaEventCreate(&a));
+    CK(cudaEventCreate(&b));
+    c->ev0.push_back(a);
+    c->ev1.push_back(b);
+  }
+  return GSGP_OK;
+}
+
+static constexpr int kGraphGenerations = 8;
+
+extern "C" gsgp_status gsgp_evolve(gsgp_ctx *c, int32_t generations, double *best_train,
+                                   double *best_test) {
+  API_GUARD(c)
+  if (c->state != 2) return fail(c, GSGP_E_STATE, "gsgp_evolve before gsgp_init");
+  if (generations < 0) return fail(c, GSGP_E_INVALID, "generations must be >= 0");
+  if (generations == 0) return GSGP_OK;
+  if ((int64_t)c->gen + generations > 0x7fffffff) return fail(c, GSGP_E_INVALID, "too many generations");
+  TRY(use_device(c));
+  TRY(ensure_trace(c, c->gen + generations));
+  const int g0 = c->gen;
+  const int bf = c->cfg.sigma_dtype == GSGP_SIGMA_BF16;
+  int left = generations;
+  if (c->timing) {
+    TRY(ensure_events(c, c->ev_used + generations));
+    const GenParams p = gen_params(c);
+    for (int k = 0; k < generations; ++k) {
+      CK(cudaEventRecord(c->ev0[c->ev_used], c->stream));
+      LAUNCH(1, launch_generation(p, bf, c->shape, c->stream));
+      CK(cudaEventRecord(c->ev1[c->ev_used], c->stream));
+      ++c->ev_used;
+    }
+    left = 0;
+  } else if (left >= kGraphGenerations) {
+    if (c->graph_dirty || !c->gexec || c->graph_u != kGraphGenerations)
+      TRY(build_graph(c, kGraphGenerations));
+    while (left >= kGraphGenerations) {
+      CK(cudaGraphLaunch(c->gexec, c->stream));
+      c->launches += kGraphGenerations;
+      left -= kGraphGenerations;
+    }
+  }
+  if (left > 0) {
+    const GenParams p = gen_params(c);
+    for (int k = 0; k < left; ++k) LAUNCH(1, launch_generation(p, bf, c->shape, c->stream));
+  }
+  c->gen += generations;
+  c->model_gen = -1;
+  if (best_train || best_test) {
+    std::vector<double2> h((size_t)generations);
+    CK(cudaMemcpyAsync(h.data(), c->best_log + g0, sizeof(double2) * (size_t)generations,
+                       cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    for (int k = 0; k < generations; ++k) {
+      if (best_train) best_train[k] = h[k].x;
+      if (best_test) best_test[k] = h[k].y;
+    }
+  }
+  return GSGP_OK;
+  API_END(c)
+}
+
+// ------------------------------------------------------- best individual --
+static gsgp_status build_model(gsgp_ctx *c) {
+  if (c->model_gen == c->gen) return GSGP_OK;
+  const int m = c->cfg.pop_size, r = c->cfg.n_random_trees;
+  const int G = c->gen;
+  if (G > c->lineage_cap) {
+    dfree(c, c->lineage);
+    int cap = 64;
+    while (cap < G) cap *= 2;
+    TRY(dalloc_n(c, &c->lineage, (size_t)cap));
+    c->lineage_cap = cap;
+  }
+  if (!c->lineage) {
+    TRY(dalloc_n(c, &c->lineage, 64));
+    c->lineage_cap = 64;
+  }
+  LAUNCH(1, launch_lineage(c->trace, m, G, c->dstate, c->lineage, c->d_anc, c->stream));
+  c->h_lineage.resize((size_t)G);
+  DevState st{};
+  if (G > 0)
+    CK(cudaMemcpyAsync(c->h_lineage.data(), c->lineage, sizeof(int4) * (size_t)G,
+                       cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaMemcpyAsync(&c->ancestor, c->d_anc, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaMemcpyAsync(&st, c->dstate, sizeof st, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  c->best_slot = st.best_slot;
+  const size_t par = (size_t)(G & 1);
+  CK(cudaMemcpyAsync(&c->best_tr, c->fit + par * m + c->best_slot, sizeof(double),
+                     cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaMemcpyAsync(&c->best_te, c->fit_te + par * m + c->best_slot, sizeof(double),
+                     cudaMemcpyDeviceToHost, c->stream));
+  // coefficients: walk generations G-1 .. 0 (+ms on rt1, -ms on rt2)
+  c->coef.assign((size_t)r, 0.0);
+  for (int g = G - 1; g >= 0; --g) {
+    const int4 e = c->h_lineage[(size_t)g];
+    if (e.y >= 0) {
+      float ms;
+      memcpy(&ms, &e.w, sizeof ms);
+      c->coef[(size_t)e.y] += (double)ms;
+      c->coef[(size_t)e.z] -= (double)ms;
+    }
+  }
+  std::vector<int> terms;
+  std::vector<double> tc;
+  for (int k = 0; k < r; ++k)
+    if (c->coef[(size_t)k] != 0.0) {
+      terms.push_back(k);
+      tc.push_back(c->coef[(size_t)k]);
+    }
+  c->n_terms = (int)terms.size();
+  if (c->n_terms > c->terms_cap || !c->d_terms) {
+    dfree(c, c->d_terms);
+    dfree(c, c->d_coef);
+    const int cap = c->n_terms > 16 ? c->n_terms : 16;
+    TRY(dalloc_n(c, &c->d_terms, (size_t)cap));
+    TRY(dalloc_n(c, &c->d_coef, (size_t)cap));
+    c->terms_cap = cap;
+  }
+  if (c->n_terms > 0) {
+    CK(cudaMemcpyAsync(c->d_terms, terms.data(), sizeof(int) * terms.size(),
+                       cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(c->d_coef, tc.data(), sizeof(double) * tc.size(), cudaMemcpyHostToDevice,
+                       c->stream));
+  }
+  CK(cudaStreamSynchronize(c->stream));
+  c->model_gen = c->gen;
+  return GSGP_OK;
+}
+
+extern "C" gsgp_status gsgp_best_trace(gsgp_ctx *c, gsgp_trace *out) {
+  API_GUARD(c)
+  if (!out || out->struct_size != sizeof(gsgp_trace))
+    return fail(c, GSGP_E_INVALID, "gsgp_trace NULL or struct_size mismatch");
+  if (c->state != 2) return fail(c, GSGP_E_STATE, "gsgp_best_trace before gsgp_init");
+  TRY(use_device(c));
+  TRY(build_model(c));
+  const int G = c->gen;
+  out->best_slot = c->best_slot;
+  out->best_train_rmse = c->best_tr;
+  out->best_test_rmse = c->best_te;
+  out->ancestor = c->ancestor;
+  out->max_genes = c->Kp;
+  out->n_generations = G;
+  out->n_random_trees = c->cfg.n_random_trees;
+  out->rt_max_genes = c->Kr;
+  out->sigma_dtype = c->cfg.sigma_dtype;
+  CK(cudaMemcpyAsync(&out->ancestor_length, c->P_len + c->ancestor, sizeof(int),
+                     cudaMemcpyDeviceToHost, c->stream));
+  if (out->ancestor_genes)
+    CK(cudaMemcpyAsync(out->ancestor_genes, c->P_genes + (size_t)c->ancestor * c->Kp,
+                       sizeof(int) * c->Kp, cudaMemcpyDeviceToHost, c->stream));
+  if (out->ancestor_consts)
+    CK(cudaMemcpyAsync(out->ancestor_consts, c->P_consts + (size_t)c->ancestor * c->Kp,
+                       sizeof(float) * c->Kp, cudaMemcpyDeviceToHost, c->stream));
+  const size_t r = (size_t)c->cfg.n_random_trees;
+  if (out->rt_genes)
+    CK(cudaMemcpyAsync(out->rt_genes, c->R_genes, sizeof(int) * r * c->Kr, cudaMemcpyDeviceToHost,
+                       c->stream));
+  if (out->rt_consts)
+    CK(cudaMemcpyAsync(out->rt_consts, c->R_consts, sizeof(float) * r * c->Kr,
+                       cudaMemcpyDeviceToHost, c->stream));
+  if (out->rt_lengths)
+    CK(cudaMemcpyAsync(out->rt_lengths, c->R_len, sizeof(int) * r, cudaMemcpyDeviceToHost,
+                       c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  for (int g = 0; g < G; ++g) {
+    const int4 e = c->h_lineage[(size_t)g];
+    if (out->lineage_parent) out->lineage_parent[g] = e.x;
+    if (out->lineage_rt1) out->lineage_rt1[g] = e.y;
+    if (out->lineage_rt2) out->lineage_rt2[g] = e.z;
+    if (out->lineage_ms) memcpy(&out->lineage_ms[g], &e.w, sizeof(float));
+  }
+  if (out->coef) memcpy(out->coef, c->coef.data(), sizeof(double) * r);
+  return GSGP_OK;
+  API_END(c)
+}
+
+static gsgp_status run_predict(gsgp_ctx *c, const float *X_dev_rows, int64_t n, double *y_dev) {
+  const int64_t n_pad = (n + 3) / 4 * 4;
+  float *Xt = nullptr;
+  TRY(dalloc_n(c, &Xt, (size_t)c->l * n_pad));
+  LAUNCH(1, launch_transpose(X_dev_rows, n, c->l, Xt, n_pad, 0, c->stream));
+  PredictParams p{};
+  p.X = Xt;
+  p.n_pad = n_pad;
+  p.n = n;
+  p.anc_genes = c->P_genes + (size_t)c->ancestor * c->Kp;
+  p.anc_consts = c->P_consts + (size_t)c->ancestor * c->Kp;
+  int anc_len = 0;
+  CK(cudaMemcpyAsync(&anc_len, c->P_len + c->ancestor, sizeof(int), cudaMemcpyDeviceToHost,
+                     c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  p.anc_len = anc_len;
+  p.rt_genes = c->R_genes;
+  p.rt_consts = c->R_consts;
+  p.rt_len = c->R_len;
+  p.Kr = c->Kr;
+  p.terms = c->d_terms;
+  p.coef = c->d_coef;
+  p.nk = c->n_terms;
+  p.y = y_dev;
+  p.protect_eps = c->cfg.protect_eps;
+  p.sigma_bf16 = c->cfg.sigma_dtype == GSGP_SIGMA_BF16;
+  LAUNCH(1, launch_predict(p, c->stream));
+  dfree(c, Xt);
+  return GSGP_OK;
+}
+
+extern "C" gsgp_status gsgp_predict(gsgp_ctx *c, const float *X, int64_t n, double *y_out) {
+  API_GUARD(c)
+  if (c->state != 2) return fail(c, GSGP_E_STATE, "gsgp_predict before gsgp_init");
+  if (n < 0 || (n > 0 && (!X || !y_out))) return fail(c, GSGP_E_INVALID, "bad predict arguments");
+  if (n == 0) return GSGP_OK;
+  if (!host_finite(X, n * c->l)) return fail(c, GSGP_E_INVALID, "non-finite value in X");
+  TRY(use_device(c));
+  TRY(build_model(c));
+  float *Xd = nullptr;
+  double *yd = nullptr;
+  TRY(dalloc_n(c, &Xd, (size_t)n * c->l));
+  TRY(dalloc_n(c, &yd, (size_t)n));
+  CK(cudaMemcpyAsync(Xd, X, sizeof(float) * (size_t)n * c->l, cudaMemcpyHostToDevice, c->stream));
+  TRY(run_predict(c, Xd, n, yd));
+  CK(cudaMemcpyAsync(y_out, yd, sizeof(double) * (size_t)n, cudaMemcpyDeviceToHost, c->stream));
+  dfree(c, Xd);
+  dfree(c, yd);
+  CK(cudaStreamSynchronize(c->stream));
+  return GSGP_OK;
+  API_END(c)
+}
+
+extern "C" gsgp_status gsgp_predict_device(gsgp_ctx *c, const float *X, int64_t n,
+                                           double *y_out) {
+  API_GUARD(c)
+  if (c->state != 2) return fail(c, GSGP_E_STATE, "gsgp_predict_device before gsgp_init");
+  if (n < 0 || (n > 0 && (!X || !y_out))) return fail(c, GSGP_E_INVALID, "bad predict arguments");
+  if (n == 0) return GSGP_OK;
+  TRY(use_device(c));
+  TRY(build_model(c));
+  TRY(run_predict(c, X, n, y_out));
+  return GSGP_OK;
+  API_END(c)
+}
+
+// ---------------------------------------------------------- introspection --
+extern "C" gsgp_status gsgp_get_info(gsgp_ctx *c, gsgp_info *out) {
+  API_GUARD(c)
+  if (!out || out->struct_size != sizeof(gsgp_info))
+    return fail(c, GSGP_E_INVALID, "gsgp_info NULL or struct_size mismatch");
+  out->state = c->state;
+  out->n_features = c->l;
+  out->n_train = c->n_tr;
+  out->n_test = c->n_te;
+  out->n_cases = c->N;
+  out->n_cases_padded = c->n_pad;
+  out->pop_size = c->cfg.pop_size;
+  out->n_random_trees = c->cfg.n_random_trees;
+  out->pop_max_genes = (1 << (c->cfg.pop_max_depth + 1)) - 1;
+  out->rt_max_genes = (1 << (c->cfg.rt_max_depth + 1)) - 1;
+  out->generation = c->gen;
+  out->evolve_tile_cases = gen_tile_cases(c->shape);
+  out->evolve_offspring_per_cta = c->shape.opb;
+  out->kernel_launches = c->launches;
+  out->device_bytes = c->dev_bytes;
+  return GSGP_OK;
+  API_END(c)
+}
+
+extern "C" gsgp_status gsgp_get_programs(gsgp_ctx *c, int32_t pool, int32_t *genes, float *consts,
+                                         int32_t *lengths) {
+  API_GUARD(c)
+  if (c->state != 2) return fail(c, GSGP_E_STATE, "programs exist after gsgp_init");
+  if (pool != GSGP_POOL_POPULATION && pool != GSGP_POOL_RANDOM)
+    return fail(c, GSGP_E_INVALID, "unknown pool");
+  TRY(use_device(c));
+  const bool P = pool == GSGP_POOL_POPULATION;
+  const size_t cnt = (size_t)(P ? c->cfg.pop_size : c->cfg.n_random_trees);
+  const size_t K = (size_t)(P ? c->Kp : c->Kr);
+  if (genes)
+    CK(cudaMemcpyAsync(genes, P ? c->P_genes : c->R_genes, sizeof(int) * cnt * K,
+                       cudaMemcpyDeviceToHost, c->stream));
+  if (consts)
+    CK(cudaMemcpyAsync(consts, P ? c->P_consts : c->R_consts, sizeof(float) * cnt * K,
+                       cudaMemcpyDeviceToHost, c->stream));
+  if (lengths)
+    CK(cudaMemcpyAsync(lengths, P ? c->P_len : c->R_len, sizeof(int) * cnt,
+                       cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return GSGP_OK;
+  API_END(c)
+}
+
+extern "C" gsgp_status gsgp_get_semantics(gsgp_ctx *c, int32_t pool, int32_t row0, int32_t rows,
+                                          float *out) {
+  API_GUARD(c)
+  if (c->state != 2) return fail(c, GSGP_E_STATE, "semantics exist after gsgp_init");
+  const bool P = pool == GSGP_POOL_POPULATION;
+  if (!P && pool != GSGP_POOL_RANDOM) return fail(c, GSGP_E_INVALID, "unknown pool");
+  const int cnt = P ? c->cfg.pop_size : c->cfg.n_random_trees;
+  if (row0 < 0 || rows < 0 || row0 + rows > cnt || (rows > 0 && !out))
+    return fail(c, GSGP_E_INVALID, "row range out of bounds");
+  if (rows == 0) return GSGP_OK;
+  TRY(use_device(c));
+  const size_t N = (size_t)c->N;
+  if (P) {
+    const int m = c->cfg.pop_size;
+    std::vector<int> rowmap((size_t)rows);
+    const size_t par = (size_t)(c->gen & 1);
+    CK(cudaMemcpyAsync(rowmap.data(), c->perm + par * 2 * m + row0, sizeof(int) * rows,
+                       cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    for (int k = 0; k < rows; ++k)
+      CK(cudaMemcpyAsync(out + (size_t)k * N, c->pool + (size_t)rowmap[(size_t)k] * c->n_pad,
+                         sizeof(float) * N, cudaMemcpyDeviceToHost, c->stream));
+  } else if (c->cfg.sigma_dtype == GSGP_SIGMA_F32) {
+    CK(cudaMemcpy2DAsync(out, sizeof(float) * N, static_cast<float *>(c->sigR) + (size_t)row0 * c->n_pad,
+                         sizeof(float) * c->n_pad, sizeof(float) * N, (size_t)rows,
+                         cudaMemcpyDeviceToHost, c->stream));
+  } else {
+    std::vector<uint16_t> h((size_t)rows * N);
+    CK(cudaMemcpy2DAsync(h.data(), 2 * N,
+                         static_cast<uint16_t *>(c->sigR) + (size_t)row0 * c->n_pad, 2 * c->n_pad,
+                         2 * N, (size_t)rows, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    for (size_t k = 0; k < h.size(); ++k) {
+      const uint32_t bits = (uint32_t)h[k] << 16;
+      memcpy(out + k, &bits, sizeof(float));
+    }
+  }
+  CK(cudaStreamSynchronize(c->stream));
+  return GSGP_OK;
+  API_END(c)
+}
+
+extern "C" gsgp_status gsgp_get_fitness(gsgp_ctx *c, double *train, double *test) {
+  API_GUARD(c)
+  if (c->state != 2) return fail(c, GSGP_E_STATE, "fitness exists after gsgp_init");
+  TRY(use_device(c));
+  const size_t m = (size_t)c->cfg.pop_size;
+  const size_t par = (size_t)(c->gen & 1);
+  if (train)
+    CK(cudaMemcpyAsync(train, c->fit + par * m, sizeof(double) * m, cudaMemcpyDeviceToHost,
+                       c->stream));
+  if (test)
+    CK(cudaMemcpyAsync(test, c->fit_te + par * m, sizeof(double) * m, cudaMemcpyDeviceToHost,
+                       c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return GSGP_OK;
+  API_END(c)
+}
+
+extern "C" gsgp_status gsgp_get_trace(gsgp_ctx *c, int32_t g0, int32_t count, int32_t *parent,
+                                      int32_t *rt1, int32_t *rt2, float *ms) {
+  API_GUARD(c)
+  if (c->state != 2) return fail(c, GSGP_E_STATE, "trace exists after gsgp_init");
+  if (g0 < 0 || count < 0 || g0 + count > c->gen)
+    return fail(c, GSGP_E_INVALID, "generation range out of bounds");
+  if (count == 0) return GSGP_OK;
+  TRY(use_device(c));
+  const size_t m = (size_t)c->cfg.pop_size;
+  std::vector<int4> h((size_t)count * m);
+  CK(cudaMemcpyAsync(h.data(), c->trace + (size_t)g0 * m, sizeof(int4) * h.size(),
+                     cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  for (size_t k = 0; k < h.size(); ++k) {
+    if (parent) parent[k] = h[k].x;
+    if (rt1) rt1[k] = h[k].y;
+    if (rt2) rt2[k] = h[k].z;
+    if (ms) memcpy(ms + k, &h[k].w, sizeof(float));
+  }
+  return GSGP_OK;
+  API_END(c)
+}
+
+extern "C" gsgp_status gsgp_set_kernel_timing(gsgp_ctx *c, int32_t enabled) {
+  API_GUARD(c)
+  c->timing = enabled != 0;
+  c->ev_used = 0;
+  return GSGP_OK;
+  API_END(c)
+}
+
+extern "C" gsgp_status gsgp_kernel_times(gsgp_ctx *c, float *ms, int32_t cap, int32_t *n_out) {
+  API_GUARD(c)
+  if (cap < 0 || (cap > 0 && !ms)) return fail(c, GSGP_E_INVALID, "bad output buffer");
+  int n = 0;
+  if (c->ev_used > 0) {
+    TRY(use_device(c));
+    CK(cudaStreamSynchronize(c->stream));
+    const int first = c->ev_used > cap ? c->ev_used - cap : 0;
+    for (int k = first; k < c->ev_used; ++k) {
+      float t = 0.f;
+      CK(cudaEventElapsedTime(&t, c->ev0[(size_t)k], c->ev1[(size_t)k]));
+      ms[n++] = t;
+    }
+  }
+  c->ev_used = 0;
+  if (n_out) *n_out = n;
+  return GSGP_OK;
+  API_END(c)
+}
+
+extern "C" gsgp_status gsgp_rng_words(uint64_t seed, uint32_t run, uint32_t gp,
+                                      uint32_t individual, int32_t n_words, uint32_t *out,
+                                      void *stream) {
+  if (n_words < 0 || (n_words > 0 && !out)) return GSGP_E_INVALID;
+  if (n_words == 0) return GSGP_OK;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  uint32_t *d = nullptr;
+  if (cudaMallocAsync((void **)&d, sizeof(uint32_t) * (size_t)n_words, s) != cudaSuccess) {
+    cudaGetLastError();
+    return GSGP_E_OOM;
+  }
+  cudaError_t e = launch_rng_words(make_uint2((uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32)),
+                                   run, gp, individual, n_words, d, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(out, d, sizeof(uint32_t) * (size_t)n_words, cudaMemcpyDeviceToHost, s);
+  cudaFreeAsync(d, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return GSGP_E_CUDA;
+  }
+  return GSGP_OK;
+}
+
+extern "C" void gsgp_destroy(gsgp_ctx *c) {
+  if (!c) return;
+  if (c->device >= 0) {
+    cudaSetDevice(c->device);
+    cudaStreamSynchronize(c->stream);
+    free_graph(c);
+    free_run_buffers(c);
+    dfree(c, c->X);
+    dfree(c, c->t);
+    dfree(c, c->d_flag);
+    for (auto e : c->ev0) cudaEventDestroy(e);
+    for (auto e : c->ev1) cudaEventDestroy(e);
+    cudaStreamSynchronize(c->stream);
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+    cudaGetLastError();
+  }
+  delete c;
+}

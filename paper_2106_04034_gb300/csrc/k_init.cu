@@ -1,0 +1,356 @@
+// Initialisation kernels of Algorithm 1: CreatePopulation (program
+// generation), ComputeSemantics (postfix interpretation over every fitness
+// case) and ComputeFitness of the initial population, plus data staging.
+#include "kernels.cuh"
+#include "reduce.cuh"
+
+namespace gsgp {
+
+// ---------------------------------------------------------------------------
+// CreatePopulation: one thread per program, ramped half-and-half in postfix.
+// Individual i of a pool with depths [dmin, dmax] (D = dmax - dmin + 1) gets
+// depth dmin + i mod D and the "full" method when floor(i / D) is even, else
+// "grow".  Nodes are decided in preorder from the individual's own Philox
+// stream: below the target depth a node is a function under "full" or at the
+// root, otherwise iff u24 < p_grow; a function draws its operator
+// idx(w, 4); a terminal is a feature idx(w, l) iff u24 < p_feature, else a
+// constant in [lo, hi).  Postfix order emits a function after both operand
+// subtrees, which the explicit frame stack below tracks without recursion.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(128)
+    treegen_kernel(int count, int dmin, int dmax, int K, int n_features, uint2 key, uint32_t run,
+                   uint32_t purpose, float p_grow, float p_feature, float lo, float hi,
+                   int *__restrict__ genes, float *__restrict__ consts, int *__restrict__ lengths) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= count) return;
+  const int D = dmax - dmin + 1;
+  const int depth = dmin + i % D;
+  const bool full = ((i / D) & 1) == 0;
+  WordStream ws(key, (uint32_t)i, kInitFlag | purpose, run);
+  int *g = genes + (size_t)i * K;
+  float *c = consts + (size_t)i * K;
+  int frame_op[kMaxDepth + 1];
+  int frame_left[kMaxDepth + 1];   // operands still to be completed
+  int sp = 0, d = 0, pos = 0;
+  for (;;) {
+    bool is_function;
+    if (d == depth)
+      is_function = false;
+    else if (full || d == 0)
+      is_function = true;
+    else
+      is_function = draw_u24(ws.next()) < p_grow;
+    if (is_function) {
+      frame_op[sp] = (int)draw_index(ws.next(), 4u);
+      frame_left[sp] = 2;
+      ++sp;
+      ++d;
+      continue;
+    }
+    if (draw_u24(ws.next()) < p_feature) {
+      const int f = (int)draw_index(ws.next(), (uint32_t)n_features);
+      g[pos] = kOpVar | (f << 8);
+      c[pos] = 0.0f;
+    } else {
+      const float v = draw_const(ws.next(), lo, hi);
+      g[pos] = kOpConst;
+      c[pos] = v;
+    }
+    ++pos;
+    // close every function whose second operand just completed
+    while (sp > 0) {
+      if (--frame_left[sp - 1] != 0) break;
+      g[pos] = frame_op[sp - 1];
+      c[pos] = 0.0f;
+      ++pos;
+      --sp;
+    }
+    if (sp == 0) break;
+    d = sp;   // next: second operand of the innermost open function
+  }
+  lengths[i] = pos;
+  for (int k = pos; k < K; ++k) {
+    g[k] = kGenePad;
+    c[k] = 0.0f;
+  }
+}
+
+cudaError_t launch_treegen(int count, int dmin, int dmax, int K, int n_features, uint2 key,
+                           uint32_t run, uint32_t purpose, float p_grow, float p_feature,
+                           float const_lo, float const_hi, int *genes, float *consts,
+                           int *lengths, cudaStream_t s) {
+  if (count <= 0) return cudaSuccess;
+  treegen_kernel<<<(count + 127) / 128, 128, 0, s>>>(count, dmin, dmax, K, n_features, key, run,
+                                                     purpose, p_grow, p_feature, const_lo,
+                                                     const_hi, genes, consts, lengths);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Row-major cases (n x l) -> feature-major X[f][col0 + j] through a padded
+// 32 x 32 shared tile, so both the reads and the writes are coalesced.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256)
+    transpose_kernel(const float *__restrict__ in, int64_t n, int l, float *__restrict__ out,
+                     int64_t n_pad, int64_t col0) {
+  __shared__ float tile[32][33];
+  const int64_t j0 = (int64_t)blockIdx.x * 32;
+  const int f0 = blockIdx.y * 32;
+  for (int k = threadIdx.y; k < 32; k += 8) {
+    const int64_t j = j0 + k;
+    const int f = f0 + threadIdx.x;
+    if (j < n && f < l) tile[k][threadIdx.x] = in[j * l + f];
+  }
+  __syncthreads();
+  for (int k = threadIdx.y; k < 32; k += 8) {
+    const int f = f0 + k;
+    const int64_t j = j0 + threadIdx.x;
+    if (j < n && f < l) out[(int64_t)f * n_pad + col0 + j] = tile[threadIdx.x][k];
+  }
+}
+
+cudaError_t launch_transpose(const float *in, int64_t n, int l, float *out, int64_t n_pad,
+                             int64_t col0, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  dim3 grid((unsigned)((n + 31) / 32), (unsigned)((l + 31) / 32));
+  transpose_kernel<<<grid, dim3(32, 8), 0, s>>>(in, n, l, out, n_pad, col0);
+  return cudaGetLastError();
+}
+
+__global__ void nonfinite_kernel(const float *__restrict__ v, int64_t n, unsigned *flag) {
+  bool bad = false;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    bad |= !isfinite(v[i]);
+  if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(flag, 1u);
+}
+
+cudaError_t launch_nonfinite_check(const float *v, int64_t n, unsigned *flag, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  const int64_t blocks = (n + 255) / 256;
+  nonfinite_kernel<<<(unsigned)(blocks < 4096 ? blocks : 4096), 256, 0, s>>>(v, n, flag);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// ComputeSemantics (Sec. 2.2, "Interpreter"): the genome is read left to
+// right with a LIFO stack; a terminal pushes, a function pops its operands
+// and pushes its result.  One CTA interprets one program over a tile of 1024
+// cases: every thread owns 4 consecutive cases (one float4 of each feature
+// row), so the gene stream is uniform across the CTA and decoded once per
+// 4 cases.  The top of the stack lives in registers; deeper entries live in
+// shared memory laid out [slot][thread] (conflict-free 16-byte accesses).
+// A function with fewer than two operands on the stack is skipped (the
+// paper's rule; generated programs never trigger it).  Protected division
+// returns 1 when |b| < eps.  Random trees are wrapped by the logistic
+// function (Sec. 2) and stored as float or bf16.  For the population the
+// CTA also reduces the squared errors of its tile (train and test cases).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float apply_op(int op, float a, float b, float eps) {
+  switch (op) {
+    case kOpAdd: return a + b;
+    case kOpSub: return a - b;
+    case kOpMul: return a * b;
+    default: return fabsf(b) < eps ? 1.0f : a / b;
+  }
+}
+
+__device__ __forceinline__ float logistic(float v) { return 1.0f / (1.0f + expf(-v)); }
+
+constexpr int kInterpThreads = 256;
+constexpr int kInterpTile = kInterpThreads * 4;
+
+template <int MODE>
+__global__ void __launch_bounds__(kInterpThreads) interpret_kernel(InterpParams p) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float4 *s_stack = reinterpret_cast<float4 *>(smem_raw);
+  int *s_gene = reinterpret_cast<int *>(s_stack + (size_t)p.stack_slots * kInterpThreads);
+  float *s_const = reinterpret_cast<float *>(s_gene + p.K);
+  __shared__ float s_red[kInterpThreads / 32][2];
+
+  const int prog = blockIdx.x;
+  const int tile = blockIdx.y;
+  const int tid = threadIdx.x;
+  const int len = p.lengths[prog];
+  for (int k = tid; k < len; k += kInterpThreads) {
+    s_gene[k] = p.genes[(size_t)prog * p.K + k];
+    s_const[k] = p.consts[(size_t)prog * p.K + k];
+  }
+  __syncthreads();
+
+  const int64_t j4 = (int64_t)tile * kInterpThreads + tid;   // float4 index
+  const bool valid = j4 * 4 < p.n_pad;
+  const int64_t jj = valid ? j4 : 0;
+  float4 tos = make_float4(0.f, 0.f, 0.f, 0.f);
+  int sp = 0;
+  for (int k = 0; k < len; ++k) {
+    const int g = s_gene[k];
+    const int op = g & 0xFF;
+    if (op >= kOpConst) {
+      float4 v;
+      if (op == kOpVar) {
+        v = __ldg(reinterpret_cast<const float4 *>(p.X + (int64_t)(g >> 8) * p.n_pad) + jj);
+      } else {
+        const float c = s_const[k];
+        v = make_float4(c, c, c, c);
+      }
+      if (sp > 0 && sp - 1 < p.stack_slots) s_stack[(sp - 1) * kInterpThreads + tid] = tos;
+      tos = v;
+      ++sp;
+    } else if (sp >= 2) {
+      const float4 a = s_stack[(sp - 2) * kInterpThreads + tid];
+      tos.x = apply_op(op, a.x, tos.x, p.protect_eps);
+      tos.y = apply_op(op, a.y, tos.y, p.protect_eps);
+      tos.z = apply_op(op, a.z, tos.z, p.protect_eps);
+      tos.w = apply_op(op, a.w, tos.w, p.protect_eps);
+      --sp;
+    }
+  }
+
+  if (MODE == 0) {
+    float str = 0.f, ste = 0.f;
+    if (valid) {
+      reinterpret_cast<float4 *>(static_cast<float *>(p.out) + (int64_t)prog * p.n_pad)[j4] = tos;
+      const float4 t = __ldg(reinterpret_cast<const float4 *>(p.target) + j4);
+      const float v[4] = {tos.x, tos.y, tos.z, tos.w};
+      const float tt[4] = {t.x, t.y, t.z, t.w};
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int64_t j = j4 * 4 + q;
+        const float d = v[q] - tt[q];
+        if (j < p.n_train)
+          str += d * d;
+        else if (j < p.n_cases)
+          ste += d * d;
+      }
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+      str += __shfl_xor_sync(0xffffffffu, str, o);
+      ste += __shfl_xor_sync(0xffffffffu, ste, o);
+    }
+    if ((tid & 31) == 0) {
+      s_red[tid >> 5][0] = str;
+      s_red[tid >> 5][1] = ste;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      double a = 0.0, b = 0.0;
+      for (int w = 0; w < kInterpThreads / 32; ++w) {
+        a += (double)s_red[w][0];
+        b += (double)s_red[w][1];
+      }
+      p.partial[(size_t)prog * p.tiles + tile] = make_double2(a, b);
+    }
+  } else if (valid) {
+    const float4 sg = make_float4(logistic(tos.x), logistic(tos.y), logistic(tos.z),
+                                  logistic(tos.w));
+    if (MODE == 1) {
+      reinterpret_cast<float4 *>(static_cast<float *>(p.out) + (int64_t)prog * p.n_pad)[j4] = sg;
+    } else {
+      __nv_bfloat162 lo = __floats2bfloat162_rn(sg.x, sg.y);
+      __nv_bfloat162 hi = __floats2bfloat162_rn(sg.z, sg.w);
+      uint2 packed;
+      packed.x = *reinterpret_cast<uint32_t *>(&lo);
+      packed.y = *reinterpret_cast<uint32_t *>(&hi);
+      reinterpret_cast<uint2 *>(static_cast<__nv_bfloat16 *>(p.out) + (int64_t)prog * p.n_pad)[j4] =
+          packed;
+    }
+  }
+}
+
+cudaError_t launch_interpret(int mode, const InterpParams &p, int count, cudaStream_t s) {
+  if (count <= 0) return cudaSuccess;
+  const size_t smem = (size_t)p.stack_slots * kInterpThreads * sizeof(float4) +
+                      (size_t)p.K * (sizeof(int) + sizeof(float));
+  dim3 grid((unsigned)count, (unsigned)((p.n_pad + kInterpTile - 1) / kInterpTile));
+  cudaError_t e = cudaSuccess;
+  switch (mode) {
+    case 0:
+      e = cudaFuncSetAttribute(interpret_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)smem);
+      if (e == cudaSuccess) interpret_kernel<0><<<grid, kInterpThreads, smem, s>>>(p);
+      break;
+    case 1:
+      e = cudaFuncSetAttribute(interpret_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)smem);
+      if (e == cudaSuccess) interpret_kernel<1><<<grid, kInterpThreads, smem, s>>>(p);
+      break;
+    default:
+      e = cudaFuncSetAttribute(interpret_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)smem);
+      if (e == cudaSuccess) interpret_kernel<2><<<grid, kInterpThreads, smem, s>>>(p);
+      break;
+  }
+  if (e != cudaSuccess) return e;
+  return cudaGetLastError();
+}
+
+// ComputeFitness of the initial population: one warp per individual sums
+// its per-tile squared errors in a fixed order and takes the RMSE.
+__global__ void __launch_bounds__(256)
+    fitness_finalize_kernel(const double2 *__restrict__ partial, int tiles, int count, int n_train,
+                            int n_test, double *__restrict__ fit, double *__restrict__ fit_te) {
+  const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (i >= count) return;
+  const double2 sse = warp_sum_partials(partial + (size_t)i * tiles, tiles, lane);
+  if (lane == 0) {
+    fit[i] = rmse_from_sse(sse.x, n_train);
+    fit_te[i] = rmse_from_sse(sse.y, n_test);
+  }
+}
+
+cudaError_t launch_fitness_finalize(const double2 *partial, int tiles, int count, int n_train,
+                                    int n_test, double *fit, double *fit_te, cudaStream_t s) {
+  if (count <= 0) return cudaSuccess;
+  fitness_finalize_kernel<<<(count * 32 + 255) / 256, 256, 0, s>>>(partial, tiles, count, n_train,
+                                                                   n_test, fit, fit_te);
+  return cudaGetLastError();
+}
+
+// Generation-0 state: population slot i lives in pool row i, offspring slot
+// i will be written to row m + i; tile counters cleared; best slot found.
+__global__ void __launch_bounds__(kFinalThreads)
+    init_state_kernel(int m, int *perm, unsigned *tile_count, const double *fit, DevState *state) {
+  __shared__ double s_v[kFinalThreads];
+  __shared__ int s_i[kFinalThreads];
+  for (int i = threadIdx.x; i < m; i += blockDim.x) {
+    perm[i] = i;
+    perm[m + i] = m + i;
+    tile_count[i] = 0u;
+  }
+  double bv;
+  int bi;
+  block_arg<false>(fit, m, s_v, s_i, bv, bi);
+  if (threadIdx.x == 0) {
+    state->gen = 0;
+    state->parity = 0;
+    state->done = 0u;
+    state->best_slot = bi;
+  }
+}
+
+cudaError_t launch_init_state(int m, int *perm, unsigned *tile_count, const double *fit,
+                              DevState *state, cudaStream_t s) {
+  init_state_kernel<<<1, kFinalThreads, 0, s>>>(m, perm, tile_count, fit, state);
+  return cudaGetLastError();
+}
+
+__global__ void rng_words_kernel(uint2 key, uint32_t run, uint32_t gp, uint32_t individual,
+                                 int n_words, uint32_t *out) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b * 4 >= n_words) return;
+  const uint4 v = philox4x32_10(make_uint4((uint32_t)b, individual, gp, run), key);
+  for (int q = 0; q < 4 && b * 4 + q < n_words; ++q) out[b * 4 + q] = lane_of(v, q);
+}
+
+cudaError_t launch_rng_words(uint2 key, uint32_t run, uint32_t gp, uint32_t individual,
+                             int n_words, uint32_t *out, cudaStream_t s) {
+  if (n_words <= 0) return cudaSuccess;
+  const int blocks = (n_words + 3) / 4;
+  rng_words_kernel<<<(blocks + 127) / 128, 128, 0, s>>>(key, run, gp, individual, n_words, out);
+  return cudaGetLastError();
+}
+
+}  // namespace gsgp

@@ -1,0 +1,67 @@
+// Host-side launchers of the GSGP kernels (each returns the CUDA launch error).
+#pragma once
+
+#include "common.cuh"
+
+namespace gsgp {
+
+// Block-wide arg-min / arg-max with the first index winning ties.
+constexpr int kFinalThreads = 256;
+
+cudaError_t launch_treegen(int count, int dmin, int dmax, int K, int n_features, uint2 key,
+                           uint32_t run, uint32_t purpose, float p_grow, float p_feature,
+                           float const_lo, float const_hi, int *genes, float *consts,
+                           int *lengths, cudaStream_t s);
+
+cudaError_t launch_transpose(const float *in, int64_t n, int l, float *out, int64_t n_pad,
+                             int64_t col0, cudaStream_t s);
+
+cudaError_t launch_nonfinite_check(const float *v, int64_t n, unsigned *flag, cudaStream_t s);
+
+// mode 0: population (float semantics + per-tile squared errors);
+// mode 1: random trees, sigma stored float; mode 2: sigma stored bf16.
+cudaError_t launch_interpret(int mode, const InterpParams &p, int count, cudaStream_t s);
+
+cudaError_t launch_fitness_finalize(const double2 *partial, int tiles, int count, int n_train,
+                                    int n_test, double *fit, double *fit_te, cudaStream_t s);
+
+cudaError_t launch_init_state(int m, int *perm, unsigned *tile_count, const double *fit,
+                              DevState *state, cudaStream_t s);
+
+// Cases per tile and offspring per CTA of the generation kernel.
+struct GenShape {
+  int vec;   // float4 chunks per thread; tile = 1024 * vec cases
+  int opb;   // offspring per CTA
+};
+int gen_tile_cases(const GenShape &sh);
+bool gen_shape_supported(const GenShape &sh);
+cudaError_t launch_generation(const GenParams &p, int sigma_bf16, const GenShape &sh,
+                              cudaStream_t s);
+
+cudaError_t launch_lineage(const int4 *trace, int m, int G, const DevState *state, int4 *lineage,
+                           int *ancestor, cudaStream_t s);
+
+struct PredictParams {
+  const float *X;      // [l][n_pad] feature-major new cases
+  int64_t n_pad;
+  int64_t n;
+  const int *anc_genes;
+  const float *anc_consts;
+  int anc_len;
+  const int *rt_genes;   // [r][Kr]
+  const float *rt_consts;
+  const int *rt_len;
+  int Kr;
+  const int *terms;      // [nk] random-tree indices with a nonzero coefficient
+  const double *coef;    // [nk]
+  int nk;
+  double *y;             // [n]
+  float protect_eps;
+  int sigma_bf16;
+};
+cudaError_t launch_predict(const PredictParams &p, cudaStream_t s);
+
+cudaError_t launch_rng_words(uint2 key, uint32_t run, uint32_t gp, uint32_t individual,
+                             int n_words, uint32_t *out, cudaStream_t s);
+
+}  // namespace gsgp

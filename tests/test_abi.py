@@ -1,0 +1,136 @@
+"""The C ABI library loads, exports every declared symbol, and its host-side
+logic (configuration checks, state machine, argument checks) works without a
+GPU.  No call here reaches the device."""
+import ctypes as C
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+import paper_2106_04034_gb300 as pkg
+from paper_2106_04034_gb300 import binding as B
+from paper_2106_04034_gb300.build import INCLUDE, build_library
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build_library()
+    return pkg.load_library()
+
+
+def declared_functions():
+    names = []
+    for h in sorted(os.listdir(INCLUDE)):
+        if not h.endswith(".h"):
+            continue
+        text = open(os.path.join(INCLUDE, h)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        names += re.findall(r"\b(gsgp_\w+)\s*\(", text)
+    return sorted(set(names))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert len(names) >= 20
+    for n in names:
+        assert hasattr(lib, n), n
+    # the binding wraps exactly the declared functions
+    assert sorted(B.exported_names()) == names
+
+
+def test_struct_layouts_match_the_header(lib, tmp_path):
+    src = tmp_path / "layout.c"
+    src.write_text("""
+#include <stdio.h>
+#include <stddef.h>
+#include "gsgp.h"
+int main(void) {
+  printf("%zu %zu %zu %zu %zu %zu %zu\\n", sizeof(gsgp_config), sizeof(gsgp_trace),
+         sizeof(gsgp_info), offsetof(gsgp_config, stream), offsetof(gsgp_trace, coef),
+         offsetof(gsgp_trace, sigma_dtype), offsetof(gsgp_info, device_bytes));
+  return 0;
+}
+""")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", INCLUDE, str(src), "-o", str(exe)], check=True)
+    got = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True,
+                                          check=True).stdout.split()]
+    want = [C.sizeof(B.Config), C.sizeof(B.Trace), C.sizeof(B.Info), B.Config.stream.offset,
+            B.Trace.coef.offset, B.Trace.sigma_dtype.offset, B.Info.device_bytes.offset]
+    assert got == want
+
+
+def test_default_config(lib):
+    cfg = pkg.default_config()
+    assert cfg.struct_size == C.sizeof(B.Config)
+    assert (cfg.pop_size, cfg.n_random_trees, cfg.tournament_size, cfg.elitism) == (1024, 1024, 4, 1)
+    assert cfg.ms == np.float32(0.1) and cfg.protect_eps == np.float32(1e-3)
+    assert cfg.p_feature_given_terminal == np.float32(0.14 / 0.18)
+    assert lib.gsgp_config_error(C.byref(cfg)) == b""
+
+
+@pytest.mark.parametrize("field,value", [
+    ("pop_size", 1), ("pop_size", 65537), ("n_random_trees", 0), ("pop_min_depth", 7),
+    ("rt_max_depth", 11), ("p_grow_function", 1.5), ("p_feature_given_terminal", -0.1),
+    ("protect_eps", -1.0), ("ms_mode", 2), ("tournament_size", 65), ("elitism", 2),
+    ("sigma_dtype", 3), ("const_lo", 5.0), ("struct_size", 8), ("ms", float("nan")),
+])
+def test_bad_configs_are_rejected(lib, field, value):
+    cfg = pkg.default_config()
+    setattr(cfg, field, value)
+    ctx = C.c_void_p()
+    assert lib.gsgp_create(C.byref(cfg), C.byref(ctx)) == B.E_INVALID
+    assert not ctx.value
+    assert lib.gsgp_config_error(C.byref(cfg)) != b""
+
+
+def test_state_machine_without_device(lib):
+    r = pkg.Run(pop_size=8, n_random_trees=4)
+    assert r.info().state == 0
+    for call in (r.init, lambda: r.evolve(3), r.best_trace, lambda: r.predict(np.zeros((2, 3))),
+                 r.fitness):
+        with pytest.raises(pkg.GsgpError) as e:
+            call()
+        assert e.value.status == B.E_STATE
+    r.close()
+    r.close()   # idempotent
+
+
+@pytest.mark.parametrize("args", [
+    dict(X=np.zeros((0, 3)), y=np.zeros(0)),                  # no training case
+    dict(X=np.array([[1.0, np.inf]]), y=np.zeros(1)),          # non-finite feature
+    dict(X=np.zeros((2, 2)), y=np.array([0.0, np.nan])),       # non-finite target
+])
+def test_bad_data_is_rejected_on_the_host(lib, args):
+    r = pkg.Run(pop_size=8, n_random_trees=4)
+    with pytest.raises(pkg.GsgpError) as e:
+        r.load(args["X"], args["y"])
+    assert e.value.status == B.E_INVALID
+    assert r.info().state == 0
+    r.close()
+
+
+def test_null_arguments(lib):
+    ctx = C.c_void_p()
+    assert lib.gsgp_create(None, C.byref(ctx)) == B.E_INVALID
+    cfg = pkg.default_config()
+    assert lib.gsgp_create(C.byref(cfg), None) == B.E_INVALID
+    assert lib.gsgp_init(None) == B.E_INVALID
+    assert lib.gsgp_last_error(None) == b""
+    lib.gsgp_destroy(None)
+    assert lib.gsgp_rng_words(1, 0, 0, 0, -1, None, None) == B.E_INVALID
+    r = pkg.Run(pop_size=8, n_random_trees=4)
+    assert lib.gsgp_load(r.ctx, None, None, 4, 2, None, None, 0) == B.E_INVALID
+    assert lib.gsgp_evolve(r.ctx, -1, None, None) in (B.E_STATE, B.E_INVALID)
+    t = B.Trace()
+    t.struct_size = 3
+    assert lib.gsgp_best_trace(r.ctx, C.byref(t)) == B.E_INVALID
+    r.close()
+
+
+def test_missing_library_fails_loudly(tmp_path, monkeypatch):
+    monkeypatch.setattr(B, "_lib", None)
+    with pytest.raises(ImportError):
+        B.load_library(str(tmp_path / "libgsgp.so"))
