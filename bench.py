@@ -36,8 +36,9 @@ import workloads as W  # noqa: E402
 
 METRIC = "semantic updates/s (pop·n·gens/s) and % of HBM peak, vs plain FP32 at stated err"
 UNIT = "semantic updates/s"
-PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "generation_kernel_mid.txt")
-GEN_KERNEL_SRC = os.path.join(ROOT, "paper_2106_04034_gb300", "csrc", "k_generation.cu")
+PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "persist_kernel_mid.txt")
+GEN_KERNEL_SRC = [os.path.join(ROOT, "paper_2106_04034_gb300", "csrc", f)
+                  for f in ("k_persist.cu", "k_generation.cu", "stream.cuh", "common.cuh")]
 
 
 def measured_peak_gbs():
@@ -49,10 +50,14 @@ def measured_peak_gbs():
 
 
 def profiled_traffic(workload_name: str):
-    """DRAM bytes per launch of the generation kernel from the committed ncu
-    summary, if it was taken on this workload with the current kernel source."""
+    """DRAM bytes per generation of the generation kernel from the committed
+    ncu summary, if it was taken on this workload with the current kernel
+    sources (else None)."""
     try:
-        src = hashlib.sha256(open(GEN_KERNEL_SRC, "rb").read()).hexdigest()[:16]
+        h = hashlib.sha256()
+        for f in GEN_KERNEL_SRC:
+            h.update(open(f, "rb").read())
+        src = h.hexdigest()[:16]
         kv = {}
         for line in open(PROFILE_SUMMARY):
             if ":" in line and not line.startswith("#"):
@@ -60,7 +65,7 @@ def profiled_traffic(workload_name: str):
                 kv[k.strip()] = v.strip()
         if kv.get("kernel_source_sha256_16") != src or kv.get("workload") != workload_name:
             return None
-        return float(kv["traffic_bytes_per_launch_full_size"])
+        return float(kv["traffic_bytes_per_generation"])
     except Exception:
         return None
 
@@ -189,13 +194,12 @@ def run_ours(args, rank, world, local_rank):
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    kernel_ms = []
     for _ in range(args.steps):
         step()
-        kernel_ms.append(run.kernel_times(1 << 20))
     e1.record(stream)
     barrier()
     clock = clocks.stop()
+    kernel_ms = [run.kernel_times(1 << 22)]
     launches = run.info().kernel_launches - launches0
     ms_total = e0.elapsed_time(e1)
     run.set_kernel_timing(False)
@@ -207,15 +211,25 @@ def run_ours(args, rank, world, local_rank):
     updates = float(w.pop_size) * w.n_cases * G
     value = updates * world / (ms_step / 1e3)
 
-    # roofline of the generation kernel: algorithmic bytes / measured duration
-    kms = np.concatenate(kernel_ms)
+    # roofline of the generation kernel: algorithmic bytes / measured duration.
+    # The persistent kernel runs up to `per` generations per launch; the
+    # chained path's stream kernel one generation per launch.
+    info = run.info()
+    per = info.evolve_generations_per_launch
+    kname = "persist_kernel" if info.evolve_path == 1 else "stream_kernel"
     sig_b = 2 if w.sigma_bf16 else 4
     ub = unique_bytes_per_generation(run, w, sig_b)
-    avg_bytes = float(ub.mean())
+    bounds = list(range(0, G, per)) + [G]
+    per_launch = np.array([ub[a:b].sum() for a, b in zip(bounds[:-1], bounds[1:])])
+    kms = np.concatenate(kernel_ms)
+    assert kms.size == per_launch.size * args.steps, (kms.size, per_launch.size)
+    total_bytes = float(per_launch.sum()) * args.steps
+    avg_bytes = total_bytes / kms.size
     avg_ms = float(kms.mean())
-    achieved = avg_bytes / (avg_ms / 1e3) / 1e9
+    achieved = total_bytes / (float(kms.sum()) / 1e3) / 1e9
     peak, peak_kind = measured_peak_gbs()
-    traffic = profiled_traffic(w.name)
+    per_gen_traffic = profiled_traffic(w.name)
+    traffic = None if per_gen_traffic is None else per_gen_traffic * G / per_launch.size
 
     # end to end through host buffers: host->device copies of the cases,
     # the whole run, prediction copied back to the host
@@ -256,11 +270,16 @@ def run_ours(args, rank, world, local_rank):
                    "l2": "working set larger than L2 (semantic matrices %.0f MB)"
                          % ((2 * w.pop_size + w.n_random_trees) * w.n_cases * 4 / 1e6),
                    "step": "load_device + init + evolve(G) + best_trace + predict(test)"},
-        "roofline": {"kernel": "generation_kernel", "bound": "hbm", "achieved": achieved,
+        "roofline": {"kernel": kname, "bound": "hbm", "achieved": achieved,
                      "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
                      "algorithmic_bytes_per_launch": avg_bytes,
-                     "avg_launch_ms": avg_ms, "launches_timed": int(kms.size)},
+                     "avg_launch_ms": avg_ms, "launches_timed": int(kms.size),
+                     "generations_per_launch": per,
+                     "shape": {"path": "persistent" if info.evolve_path == 1 else "chained",
+                               "tile_cases": info.evolve_tile_cases,
+                               "offspring_per_cta": info.evolve_offspring_per_cta,
+                               "grid": info.evolve_grid}},
         "e2e": {"value": updates * world / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h)},
         "gpu_launches": int(launches),

@@ -144,6 +144,10 @@ gsgp_status gsgp_load_device(gsgp_ctx *ctx, const float *X_train, const float *y
  * GSGP_E_OOM, GSGP_E_CUDA. */
 gsgp_status gsgp_init(gsgp_ctx *ctx);
 
+/* Errors of every call that synchronises after device work also include
+ * GSGP_E_TIMEOUT: a bounded wait of the persistent generation kernel gave up
+ * (never expected; the run must be restarted with gsgp_init). */
+
 /* Run `generations` generations of the loop of Algorithm 1 (GSM, fitness of
  * the offspring, survival with elitism), continuing from the current one.
  * best_train_rmse / best_test_rmse (nullable HOST arrays of `generations`
@@ -216,8 +220,12 @@ typedef struct {
   int32_t pop_size, n_random_trees;
   int32_t pop_max_genes, rt_max_genes;
   int32_t generation;                 /* generations run since init */
-  int32_t evolve_tile_cases;          /* cases per tile of the generation kernel */
+  int32_t evolve_tile_cases;          /* cases per tile of the mutation stream (0 before
+                                         the first gsgp_evolve chose a shape) */
   int32_t evolve_offspring_per_cta;
+  int32_t evolve_path;                /* GSGP_PATH_PERSISTENT or GSGP_PATH_CHAINED */
+  int32_t evolve_grid;                /* CTAs of the persistent kernel */
+  int32_t evolve_generations_per_launch;
   int64_t kernel_launches;            /* library kernels launched since create */
   int64_t device_bytes;               /* device memory held by the context */
 } gsgp_info;
@@ -246,11 +254,32 @@ gsgp_status gsgp_get_fitness(gsgp_ctx *ctx, double *train, double *test);
 gsgp_status gsgp_get_trace(gsgp_ctx *ctx, int32_t g0, int32_t count, int32_t *parent,
                            int32_t *rt1, int32_t *rt2, float *ms);
 
-/* Kernel timing of the generation kernel.  When enabled, gsgp_evolve
- * records CUDA events around every launch of the fused generation kernel on
- * config.stream; gsgp_kernel_times then synchronises and returns the
- * durations (ms) of the most recent min(cap, n) launches, oldest first, and
- * clears them.  *n_out receives the count. */
+/* How generations run on the device.
+ *   GSGP_PATH_PERSISTENT: one cooperative kernel runs up to 64 generations
+ *     per launch, its CTAs resident throughout and synchronised by grid-wide
+ *     barriers (3 per generation); the default where cooperative launch is
+ *     available.
+ *   GSGP_PATH_CHAINED: three launches per generation (selection, mutation
+ *     stream, fitness + survival) chained with programmatic dependent launch
+ *     and replayed from a CUDA graph.
+ * Both produce bit-identical results.  The shape of the mutation stream is
+ * (vec, opb): a tile of 1024 * vec cases for opb offspring per CTA
+ * (persistent: vec in {1,2}, opb in {1,2,4}; chained: vec in {1,2,4},
+ * opb in {2,4,8}).  path 0 chooses the path; vec = opb = 0 (the default)
+ * times every supported shape of the path on the first gsgp_evolve of a
+ * problem layout and keeps the fastest for the process.  Results do not
+ * depend on the path or the shape.  Errors: GSGP_E_INVALID. */
+enum { GSGP_PATH_AUTO = 0, GSGP_PATH_PERSISTENT = 1, GSGP_PATH_CHAINED = 2 };
+gsgp_status gsgp_set_evolve_shape(gsgp_ctx *ctx, int32_t path, int32_t vec, int32_t opb);
+
+/* Timing of the generation kernel.  When enabled, gsgp_evolve records CUDA
+ * events on config.stream right before and after every launch of the
+ * dominant kernel: the persistent kernel (one launch per up to 64
+ * generations, see gsgp_info.evolve_generations_per_launch) or, on the
+ * chained path, the mutation stream kernel of each generation.
+ * gsgp_kernel_times then synchronises and returns the durations (ms) of the
+ * most recent min(cap, n) launches, oldest first, and clears them.  *n_out
+ * receives the count. */
 gsgp_status gsgp_set_kernel_timing(gsgp_ctx *ctx, int32_t enabled);
 gsgp_status gsgp_kernel_times(gsgp_ctx *ctx, float *ms, int32_t cap, int32_t *n_out);
 

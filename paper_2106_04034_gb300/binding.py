@@ -22,6 +22,7 @@ OK, E_INVALID, E_STATE, E_OOM, E_CUDA, E_TIMEOUT, E_NUMERIC = range(7)
 OP_ADD, OP_SUB, OP_MUL, OP_DIV, OP_CONST, OP_VAR, GENE_PAD = 0, 1, 2, 3, 4, 5, -1
 SIGMA_F32, SIGMA_BF16 = 0, 1
 POOL_POPULATION, POOL_RANDOM = 0, 1
+PATH_AUTO, PATH_PERSISTENT, PATH_CHAINED = 0, 1, 2
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p)
 FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p, C.c_void_p)
@@ -71,6 +72,8 @@ class Info(C.Structure):
         ("n_cases_padded", C.c_int64), ("pop_size", C.c_int32), ("n_random_trees", C.c_int32),
         ("pop_max_genes", C.c_int32), ("rt_max_genes", C.c_int32), ("generation", C.c_int32),
         ("evolve_tile_cases", C.c_int32), ("evolve_offspring_per_cta", C.c_int32),
+        ("evolve_path", C.c_int32), ("evolve_grid", C.c_int32),
+        ("evolve_generations_per_launch", C.c_int32),
         ("kernel_launches", C.c_int64), ("device_bytes", C.c_int64),
     ]
 
@@ -94,6 +97,7 @@ _SIGS = {
     "gsgp_get_semantics": (C.c_int, [P, C.c_int32, C.c_int32, C.c_int32, P]),
     "gsgp_get_fitness": (C.c_int, [P, P, P]),
     "gsgp_get_trace": (C.c_int, [P, C.c_int32, C.c_int32, P, P, P, P]),
+    "gsgp_set_evolve_shape": (C.c_int, [P, C.c_int32, C.c_int32, C.c_int32]),
     "gsgp_set_kernel_timing": (C.c_int, [P, C.c_int32]),
     "gsgp_kernel_times": (C.c_int, [P, P, C.c_int32, P]),
     "gsgp_rng_words": (C.c_int, [C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint32, C.c_int32, P, P]),
@@ -327,6 +331,9 @@ class Run:
         self._check(self.lib.gsgp_get_trace(self.ctx, g0, count, _ptr(a[0]), _ptr(a[1]),
                                             _ptr(a[2]), _ptr(ms)))
         return a[0], a[1], a[2], ms
+
+    def set_evolve_shape(self, path: int, vec: int = 0, opb: int = 0):
+        self._check(self.lib.gsgp_set_evolve_shape(self.ctx, path, vec, opb))
 
     def set_kernel_timing(self, enabled: bool):
         self._check(self.lib.gsgp_set_kernel_timing(self.ctx, int(enabled)))

@@ -4,6 +4,7 @@
 // k_init.cu, k_generation.cu and k_predict.cu.
 #include <cmath>
 #include <cstdarg>
+#include <cstddef>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -32,8 +33,22 @@ struct gsgp_ctx {
 
   // run state
   int Kp = 0, Kr = 0;
-  int tiles_interp = 0, tiles_gen = 0;
-  GenShape shape{2, 4};
+  int tiles_interp = 0;   // 1024-case chunks of a semantic row
+  // generation loop: path 1 = persistent cooperative kernel, 2 = chained
+  // select/stream/final launches; shape = (float4 chunks per thread,
+  // offspring per CTA); grid = CTAs of the persistent kernel
+  int path = 1;
+  GenShape shape{1, 2};
+  int grid = 0;
+  int forced_path = 0;       // gsgp_set_evolve_shape: 0 = choose
+  GenShape forced{0, 0};     // {0, 0} = autotune within the path
+  bool shape_ready = false;
+  GridSync *gs = nullptr;
+  ulonglong2 *cta_min = nullptr, *cta_max = nullptr;
+  int cta_cap = 0;
+  int *bk_perm = nullptr;    // state snapshot used while autotuning
+  double *bk_fit = nullptr, *bk_fit_te = nullptr;
+  DevState *bk_state = nullptr;
   int64_t layout_key[7] = {0, 0, 0, 0, 0, 0, 0};
   int *P_genes = nullptr, *P_len = nullptr, *R_genes = nullptr, *R_len = nullptr;
   float *P_consts = nullptr, *R_consts = nullptr;
@@ -42,7 +57,8 @@ struct gsgp_ctx {
   int *perm = nullptr;
   double *fit = nullptr, *fit_te = nullptr;
   double2 *partial = nullptr;
-  unsigned *tile_count = nullptr;
+  int4 *sel = nullptr;
+  float *sel_ms = nullptr;
   DevState *dstate = nullptr;
   int4 *trace = nullptr;
   double2 *best_log = nullptr;
@@ -53,12 +69,17 @@ struct gsgp_ctx {
   unsigned *d_flag = nullptr;
   int gen = 0;
 
-  // CUDA graph of `graph_u` generations, replayed by gsgp_evolve
+  // CUDA graph of `graph_u` generations, replayed by gsgp_evolve; when built
+  // for timing it records an event before and after every stream launch
+  cudaGraph_t graph = nullptr;
   cudaGraphExec_t gexec = nullptr;
   int graph_u = 0;
+  bool graph_timed = false;
   bool graph_dirty = true;
+  std::vector<cudaGraphNode_t> ev_nodes;   // [2 * graph_u] start/stop record nodes
+  std::vector<cudaEvent_t> ev_marks;       // events the nodes were captured with
 
-  // generation-kernel timing
+  // stream-kernel timing
   bool timing = false;
   std::vector<cudaEvent_t> ev0, ev1;
   int ev_used = 0;
@@ -187,8 +208,17 @@ static void free_run_buffers(gsgp_ctx *c) {
   dfree(c, c->fit);
   dfree(c, c->fit_te);
   dfree(c, c->partial);
-  dfree(c, c->tile_count);
+  dfree(c, c->sel);
+  dfree(c, c->sel_ms);
   dfree(c, c->dstate);
+  dfree(c, c->gs);
+  dfree(c, c->cta_min);
+  dfree(c, c->cta_max);
+  dfree(c, c->bk_perm);
+  dfree(c, c->bk_fit);
+  dfree(c, c->bk_fit_te);
+  dfree(c, c->bk_state);
+  c->cta_cap = 0;
   dfree(c, c->trace);
   dfree(c, c->best_log);
   dfree(c, c->lineage);
@@ -204,8 +234,11 @@ static void free_run_buffers(gsgp_ctx *c) {
 
 static void free_graph(gsgp_ctx *c) {
   if (c->gexec) cudaGraphExecDestroy(c->gexec);
+  if (c->graph) cudaGraphDestroy(c->graph);
   c->gexec = nullptr;
+  c->graph = nullptr;
   c->graph_u = 0;
+  c->ev_nodes.clear();
 }
 
 // ---------------------------------------------------------------- config --
@@ -401,7 +434,8 @@ static GenParams gen_params(gsgp_ctx *c) {
   p.fit = c->fit;
   p.fit_te = c->fit_te;
   p.partial = c->partial;
-  p.tile_count = c->tile_count;
+  p.sel = c->sel;
+  p.sel_ms = c->sel_ms;
   p.trace = c->trace;
   p.best_log = c->best_log;
   p.state = c->dstate;
@@ -411,7 +445,7 @@ static GenParams gen_params(gsgp_ctx *c) {
   p.tsize = c->cfg.tournament_size;
   p.n_train = (int)c->n_tr;
   p.n_cases = (int)c->N;
-  p.tiles = c->tiles_gen;
+  p.tiles = c->tiles_interp;   // 1024-case chunks, whatever the stream shape
   p.ms_mode = c->cfg.ms_mode;
   p.ms = c->cfg.ms;
   p.key = make_uint2((uint32_t)(c->cfg.seed & 0xffffffffu), (uint32_t)(c->cfg.seed >> 32));
@@ -452,15 +486,14 @@ extern "C" gsgp_status gsgp_init(gsgp_ctx *c) {
   const int m = cf.pop_size, r = cf.n_random_trees;
   const int Kp = (1 << (cf.pop_max_depth + 1)) - 1;
   const int Kr = (1 << (cf.rt_max_depth + 1)) - 1;
-  const int W = gen_tile_cases(c->shape);
-  const int64_t key[7] = {m, r, c->n_pad, Kp, Kr, cf.sigma_dtype, W};
+  const int64_t key[7] = {m, r, c->n_pad, Kp, Kr, cf.sigma_dtype, 0};
   if (memcmp(key, c->layout_key, sizeof key) != 0) {
     free_run_buffers(c);
     c->Kp = Kp;
     c->Kr = Kr;
+    // partial sums per 1024-case chunk (interpreter and stream kernels)
     c->tiles_interp = (int)((c->n_pad + 1023) / 1024);
-    c->tiles_gen = (int)((c->n_pad + W - 1) / W);
-    const int tiles_max = c->tiles_interp > c->tiles_gen ? c->tiles_interp : c->tiles_gen;
+    const int tiles_max = c->tiles_interp;
     TRY(dalloc_n(c, &c->P_genes, (size_t)m * Kp));
     TRY(dalloc_n(c, &c->P_consts, (size_t)m * Kp));
     TRY(dalloc_n(c, &c->P_len, (size_t)m));
@@ -474,11 +507,13 @@ extern "C" gsgp_status gsgp_init(gsgp_ctx *c) {
     TRY(dalloc_n(c, &c->fit, (size_t)2 * m));
     TRY(dalloc_n(c, &c->fit_te, (size_t)2 * m));
     TRY(dalloc_n(c, &c->partial, (size_t)m * tiles_max));
-    TRY(dalloc_n(c, &c->tile_count, (size_t)m));
+    TRY(dalloc_n(c, &c->sel, (size_t)m));
+    TRY(dalloc_n(c, &c->sel_ms, (size_t)m));
     TRY(dalloc_n(c, &c->dstate, 1));
     TRY(dalloc_n(c, &c->d_anc, 1));
     memcpy(c->layout_key, key, sizeof key);
     c->graph_dirty = true;
+    c->shape_ready = false;
   }
   c->gen = 0;
   c->model_gen = -1;
@@ -520,35 +555,277 @@ extern "C" gsgp_status gsgp_init(gsgp_ctx *c) {
   LAUNCH(1, launch_interpret(cf.sigma_dtype == GSGP_SIGMA_BF16 ? 2 : 1, ip, r, c->stream));
   LAUNCH(1, launch_fitness_finalize(c->partial, c->tiles_interp, m, (int)c->n_tr, (int)c->n_te,
                                     c->fit, c->fit_te, c->stream));
-  LAUNCH(1, launch_init_state(m, c->perm, c->tile_count, c->fit, c->dstate, c->stream));
+  LAUNCH(1, launch_init_state(m, c->perm, c->fit, c->dstate, c->stream));
+  if (c->gs) CK(cudaMemsetAsync(&c->gs->err, 0, sizeof(int), c->stream));
   c->state = 2;
   return GSGP_OK;
   API_END(c)
 }
 
 // ---------------------------------------------------------------- evolve --
-static gsgp_status build_graph(gsgp_ctx *c, int u) {
+static gsgp_status launch_generation(gsgp_ctx *c, const GenParams &p, cudaStream_t s,
+                                     cudaEvent_t ev_start, cudaEvent_t ev_stop, bool external) {
+  const int bf = c->cfg.sigma_dtype == GSGP_SIGMA_BF16;
+  LAUNCH(1, launch_select(p, s, true));
+  if (ev_start)
+    CK(external ? cudaEventRecordWithFlags(ev_start, s, cudaEventRecordExternal)
+                : cudaEventRecord(ev_start, s));
+  LAUNCH(1, launch_stream(p, bf, c->shape, s, ev_start == nullptr));
+  if (ev_stop)
+    CK(external ? cudaEventRecordWithFlags(ev_stop, s, cudaEventRecordExternal)
+                : cudaEventRecord(ev_stop, s));
+  LAUNCH(1, launch_final(p, s, ev_stop == nullptr));
+  return GSGP_OK;
+}
+
+// Shapes the autotuner tries: chained path (vec in {1,2,4}, opb in {2,4,8})
+// and persistent path (vec in {1,2}, opb in {1,2,4}); the choice is cached
+// per problem layout for the process.
+static const GenShape kChainShapes[] = {{1, 2}, {1, 4}, {1, 8}, {2, 2}, {2, 4},
+                                        {2, 8}, {4, 2}, {4, 4}, {4, 8}};
+static const GenShape kPersistShapes[] = {{1, 1}, {1, 2}, {1, 4}, {2, 1}, {2, 2}, {2, 4}};
+struct Tuned {
+  int path;
+  GenShape shape;
+};
+static std::unordered_map<std::string, Tuned> g_tuned;
+
+static std::string shape_key(gsgp_ctx *c) {
+  char buf[192];
+  snprintf(buf, sizeof buf, "%d:%d:%d:%lld:%d:%lld:%d:%d:%d", c->device, c->cfg.pop_size,
+           c->cfg.n_random_trees, (long long)c->n_pad, c->cfg.sigma_dtype, (long long)c->n_tr,
+           c->forced_path, c->forced.vec, c->forced.opb);
+  return buf;
+}
+
+// CTAs of the persistent kernel: at most the co-resident count, and no more
+// than needed to give every CTA the same number of stream items (a partly
+// filled last round of items would leave most CTAs idle at the barrier).
+static int persist_grid(gsgp_ctx *c, const GenShape &sh) {
+  const int max_grid = persist_max_grid(c->cfg.sigma_dtype == GSGP_SIGMA_BF16, sh);
+  if (max_grid <= 0) return 0;
+  const int64_t tiles = (c->n_pad + 1024 * sh.vec - 1) / (1024 * sh.vec);
+  const int64_t groups = (c->cfg.pop_size + sh.opb - 1) / sh.opb;
+  const int64_t items = tiles * groups;
+  const int64_t rounds = (items + max_grid - 1) / max_grid;
+  const int64_t grid = (items + rounds - 1) / rounds;
+  return (int)(grid < max_grid ? grid : max_grid);
+}
+
+static gsgp_status ensure_cta_arrays(gsgp_ctx *c, int grid) {
+  if (grid <= c->cta_cap && c->gs) return GSGP_OK;
+  int err = 0;
+  if (c->gs) {   // keep the sticky error word across the reallocation
+    CK(cudaMemcpyAsync(&err, &c->gs->err, sizeof err, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+  }
+  dfree(c, c->cta_min);
+  dfree(c, c->cta_max);
+  dfree(c, c->gs);
+  TRY(dalloc_n(c, &c->cta_min, (size_t)grid));
+  TRY(dalloc_n(c, &c->cta_max, (size_t)grid));
+  void *g = nullptr;
+  TRY(dalloc(c, &g, grid_sync_bytes(grid)));
+  c->gs = static_cast<GridSync *>(g);
+  CK(cudaMemsetAsync(c->gs, 0, grid_sync_bytes(grid), c->stream));
+  if (err) CK(cudaMemcpyAsync(&c->gs->err, &err, sizeof err, cudaMemcpyHostToDevice, c->stream));
+  c->cta_cap = grid;
+  return GSGP_OK;
+}
+
+static gsgp_status launch_persist_chunk(gsgp_ctx *c, int G) {
+  const GenParams p = gen_params(c);
+  PersistArgs x{c->gs, c->cta_min, c->cta_max, G};
+  CK(cudaMemsetAsync(&c->gs->count, 0, grid_sync_bytes(c->grid) - offsetof(GridSync, count),
+                     c->stream));
+  LAUNCH(1, launch_persist(p, x, c->cfg.sigma_dtype == GSGP_SIGMA_BF16, c->shape, c->grid,
+                           c->stream));
+  return GSGP_OK;
+}
+
+// Save / restore the per-generation state (slot-to-row map, fitness,
+// counters) around autotuning trials of whole generations.  A trial of one
+// generation writes only free rows of the pool, the draws, the partials and
+// this generation's trace and log entries, all of which the real generation
+// rewrites identically.
+static gsgp_status snapshot(gsgp_ctx *c, bool save) {
+  const size_t m = (size_t)c->cfg.pop_size;
+  if (!c->bk_perm) {
+    TRY(dalloc_n(c, &c->bk_perm, 4 * m));
+    TRY(dalloc_n(c, &c->bk_fit, 2 * m));
+    TRY(dalloc_n(c, &c->bk_fit_te, 2 * m));
+    TRY(dalloc_n(c, &c->bk_state, 1));
+  }
+  const cudaMemcpyKind k = cudaMemcpyDeviceToDevice;
+  if (save) {
+    CK(cudaMemcpyAsync(c->bk_perm, c->perm, sizeof(int) * 4 * m, k, c->stream));
+    CK(cudaMemcpyAsync(c->bk_fit, c->fit, sizeof(double) * 2 * m, k, c->stream));
+    CK(cudaMemcpyAsync(c->bk_fit_te, c->fit_te, sizeof(double) * 2 * m, k, c->stream));
+    CK(cudaMemcpyAsync(c->bk_state, c->dstate, sizeof(DevState), k, c->stream));
+  } else {
+    CK(cudaMemcpyAsync(c->perm, c->bk_perm, sizeof(int) * 4 * m, k, c->stream));
+    CK(cudaMemcpyAsync(c->fit, c->bk_fit, sizeof(double) * 2 * m, k, c->stream));
+    CK(cudaMemcpyAsync(c->fit_te, c->bk_fit_te, sizeof(double) * 2 * m, k, c->stream));
+    CK(cudaMemcpyAsync(c->dstate, c->bk_state, sizeof(DevState), k, c->stream));
+  }
+  return GSGP_OK;
+}
+
+static gsgp_status time_shape(gsgp_ctx *c, int path, const GenShape &sh, float *out_ms) {
+  const int bf = c->cfg.sigma_dtype == GSGP_SIGMA_BF16;
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  c->path = path;
+  c->shape = sh;
+  gsgp_status st = GSGP_OK;
+  cudaError_t e = cudaSuccess;
+  float best = 1e30f;
+  if (path == 2) {
+    const GenParams p = gen_params(c);
+    e = launch_select(p, c->stream, false);
+    for (int rep = 0; rep < 4 && e == cudaSuccess; ++rep) {
+      if (e == cudaSuccess) e = cudaEventRecord(e0, c->stream);
+      if (e == cudaSuccess) e = launch_stream(p, bf, sh, c->stream, false);
+      if (e == cudaSuccess) e = cudaEventRecord(e1, c->stream);
+      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+      float ms = 0.f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+      if (e == cudaSuccess && rep > 0 && ms < best) best = ms;
+      c->launches += 1;
+    }
+    c->launches += 1;
+  } else {
+    c->grid = persist_grid(c, sh);
+    st = ensure_cta_arrays(c, c->grid);
+    if (st == GSGP_OK) st = snapshot(c, true);
+    for (int rep = 0; rep < 4 && st == GSGP_OK && e == cudaSuccess; ++rep) {
+      e = cudaEventRecord(e0, c->stream);
+      if (e == cudaSuccess) st = launch_persist_chunk(c, 1);
+      if (st == GSGP_OK && e == cudaSuccess) e = cudaEventRecord(e1, c->stream);
+      if (st == GSGP_OK && e == cudaSuccess) st = snapshot(c, false);
+      if (st == GSGP_OK && e == cudaSuccess) e = cudaEventSynchronize(e1);
+      float ms = 0.f;
+      if (st == GSGP_OK && e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+      if (rep > 0 && ms > 0.f && ms < best) best = ms;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != GSGP_OK) return st;
+  if (e != cudaSuccess) return cuda_fail(c, e, "autotune", __LINE__);
+  *out_ms = best;
+  return GSGP_OK;
+}
+
+// Choose the generation path and shape: forced, cached for this layout, or
+// timed.  The persistent path is used whenever the device supports
+// cooperative launch (it removes the per-generation launch chain); a forced
+// path may still autotune its shape.
+static gsgp_status choose_shape(gsgp_ctx *c) {
+  if (c->shape_ready) return GSGP_OK;
+  const int bf = c->cfg.sigma_dtype == GSGP_SIGMA_BF16;
+  int path = c->forced_path;
+  if (path == 0) path = persist_max_grid(bf, GenShape{1, 2}) > 0 ? 1 : 2;
+  if (c->forced.vec) {
+    c->path = path;
+    c->shape = c->forced;
+  } else {
+    const std::string key = shape_key(c);
+    auto it = g_tuned.find(key);
+    if (it != g_tuned.end()) {
+      c->path = it->second.path;
+      c->shape = it->second.shape;
+    } else {
+      float best_ms = 1e30f;
+      Tuned best{path, path == 1 ? kPersistShapes[0] : kChainShapes[0]};
+      const GenShape *cand = path == 1 ? kPersistShapes : kChainShapes;
+      const int nc = path == 1 ? (int)(sizeof kPersistShapes / sizeof kPersistShapes[0])
+                               : (int)(sizeof kChainShapes / sizeof kChainShapes[0]);
+      for (int k = 0; k < nc; ++k) {
+        if (path == 1 && persist_max_grid(bf, cand[k]) <= 0) continue;
+        float ms = 0.f;
+        TRY(time_shape(c, path, cand[k], &ms));
+        if (ms < best_ms) {
+          best_ms = ms;
+          best = Tuned{path, cand[k]};
+        }
+      }
+      g_tuned[key] = best;
+      c->path = best.path;
+      c->shape = best.shape;
+    }
+  }
+  if (c->path == 1) {
+    c->grid = persist_grid(c, c->shape);
+    if (c->grid <= 0) return fail(c, GSGP_E_CUDA, "cooperative launch is not available");
+    TRY(ensure_cta_arrays(c, c->grid));
+  }
+  c->shape_ready = true;
+  c->graph_dirty = true;
+  return GSGP_OK;
+}
+
+// Sticky device error of the persistent kernel's barrier (after a sync).
+static gsgp_status check_device_error(gsgp_ctx *c) {
+  if (!c->gs) return GSGP_OK;
+  int err = 0;
+  CK(cudaMemcpyAsync(&err, &c->gs->err, sizeof err, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  if (err)
+    return fail(c, GSGP_E_TIMEOUT,
+                "a grid barrier of the generation kernel gave up waiting; re-run gsgp_init");
+  return GSGP_OK;
+}
+
+static gsgp_status build_graph(gsgp_ctx *c, int u, bool timed) {
   free_graph(c);
   if (!c->cap_stream) CK(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+  while (timed && (int)c->ev_marks.size() < 2 * u) {
+    cudaEvent_t e;
+    CK(cudaEventCreate(&e));
+    c->ev_marks.push_back(e);
+  }
   const GenParams p = gen_params(c);
   CK(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
-  cudaError_t le = cudaSuccess;
-  for (int k = 0; k < u && le == cudaSuccess; ++k)
-    le = launch_generation(p, c->cfg.sigma_dtype == GSGP_SIGMA_BF16, c->shape, c->cap_stream);
+  gsgp_status st = GSGP_OK;
+  for (int k = 0; k < u && st == GSGP_OK; ++k)
+    st = launch_generation(c, p, c->cap_stream, timed ? c->ev_marks[2 * k] : nullptr,
+                           timed ? c->ev_marks[2 * k + 1] : nullptr, true);
   cudaGraph_t graph = nullptr;
   cudaError_t ee = cudaStreamEndCapture(c->cap_stream, &graph);
-  if (le != cudaSuccess) {
+  if (st != GSGP_OK) {
     if (graph) cudaGraphDestroy(graph);
-    return cuda_fail(c, le, "launch_generation (capture)", __LINE__);
+    return st;
   }
   if (ee != cudaSuccess) return cuda_fail(c, ee, "cudaStreamEndCapture", __LINE__);
+  c->graph = graph;
+  if (timed) {
+    // locate the event-record nodes by the event each was captured with
+    c->ev_nodes.assign((size_t)2 * u, nullptr);
+    size_t n = 0;
+    CK(cudaGraphGetNodes(graph, nullptr, &n));
+    std::vector<cudaGraphNode_t> nodes(n);
+    CK(cudaGraphGetNodes(graph, nodes.data(), &n));
+    for (cudaGraphNode_t nd : nodes) {
+      cudaGraphNodeType ty;
+      CK(cudaGraphNodeGetType(nd, &ty));
+      if (ty != cudaGraphNodeTypeEventRecord) continue;
+      cudaEvent_t ev;
+      CK(cudaGraphEventRecordNodeGetEvent(nd, &ev));
+      for (int k = 0; k < 2 * u; ++k)
+        if (c->ev_marks[(size_t)k] == ev) c->ev_nodes[(size_t)k] = nd;
+    }
+    for (auto nd : c->ev_nodes)
+      if (!nd) return fail(c, GSGP_E_CUDA, "timing node missing from the captured graph");
+  }
   cudaError_t ie = cudaGraphInstantiate(&c->gexec, graph, 0);
-  cudaGraphDestroy(graph);
   if (ie != cudaSuccess) {
     c->gexec = nullptr;
     return cuda_fail(c, ie, "cudaGraphInstantiate", __LINE__);
   }
   c->graph_u = u;
+  c->graph_timed = timed;
   c->graph_dirty = false;
   return GSGP_OK;
 }
@@ -564,7 +841,8 @@ static gsgp_status ensure_events(gsgp_ctx *c, int need) {
   return GSGP_OK;
 }
 
-static constexpr int kGraphGenerations = 8;
+static constexpr int kGraphGenerations = 8;      // chained path: generations per graph
+static constexpr int kPersistGenerations = 64;   // persistent path: generations per launch
 
 extern "C" gsgp_status gsgp_evolve(gsgp_ctx *c, int32_t generations, double *best_train,
                                    double *best_test) {
@@ -575,31 +853,52 @@ extern "C" gsgp_status gsgp_evolve(gsgp_ctx *c, int32_t generations, double *bes
   if ((int64_t)c->gen + generations > 0x7fffffff) return fail(c, GSGP_E_INVALID, "too many generations");
   TRY(use_device(c));
   TRY(ensure_trace(c, c->gen + generations));
+  TRY(choose_shape(c));
   const int g0 = c->gen;
-  const int bf = c->cfg.sigma_dtype == GSGP_SIGMA_BF16;
   int left = generations;
-  if (c->timing) {
-    TRY(ensure_events(c, c->ev_used + generations));
-    const GenParams p = gen_params(c);
-    for (int k = 0; k < generations; ++k) {
-      CK(cudaEventRecord(c->ev0[c->ev_used], c->stream));
-      LAUNCH(1, launch_generation(p, bf, c->shape, c->stream));
-      CK(cudaEventRecord(c->ev1[c->ev_used], c->stream));
-      ++c->ev_used;
+  if (c->timing) TRY(ensure_events(c, c->ev_used + generations));
+  if (c->path == 1) {
+    while (left > 0) {
+      const int G = left < kPersistGenerations ? left : kPersistGenerations;
+      if (c->timing) CK(cudaEventRecord(c->ev0[(size_t)c->ev_used], c->stream));
+      TRY(launch_persist_chunk(c, G));
+      if (c->timing) {
+        CK(cudaEventRecord(c->ev1[(size_t)c->ev_used], c->stream));
+        ++c->ev_used;
+      }
+      left -= G;
     }
-    left = 0;
-  } else if (left >= kGraphGenerations) {
-    if (c->graph_dirty || !c->gexec || c->graph_u != kGraphGenerations)
-      TRY(build_graph(c, kGraphGenerations));
+  }
+  if (left >= kGraphGenerations) {
+    if (c->graph_dirty || !c->gexec || c->graph_u != kGraphGenerations ||
+        c->graph_timed != c->timing)
+      TRY(build_graph(c, kGraphGenerations, c->timing));
     while (left >= kGraphGenerations) {
+      if (c->timing) {
+        for (int k = 0; k < kGraphGenerations; ++k) {
+          CK(cudaGraphExecEventRecordNodeSetEvent(c->gexec, c->ev_nodes[(size_t)2 * k],
+                                                  c->ev0[(size_t)c->ev_used + k]));
+          CK(cudaGraphExecEventRecordNodeSetEvent(c->gexec, c->ev_nodes[(size_t)2 * k + 1],
+                                                  c->ev1[(size_t)c->ev_used + k]));
+        }
+        c->ev_used += kGraphGenerations;
+      }
       CK(cudaGraphLaunch(c->gexec, c->stream));
-      c->launches += kGraphGenerations;
+      c->launches += 3 * kGraphGenerations;
       left -= kGraphGenerations;
     }
   }
   if (left > 0) {
     const GenParams p = gen_params(c);
-    for (int k = 0; k < left; ++k) LAUNCH(1, launch_generation(p, bf, c->shape, c->stream));
+    for (int k = 0; k < left; ++k) {
+      cudaEvent_t a = nullptr, b = nullptr;
+      if (c->timing) {
+        a = c->ev0[(size_t)c->ev_used];
+        b = c->ev1[(size_t)c->ev_used];
+        ++c->ev_used;
+      }
+      TRY(launch_generation(c, p, c->stream, a, b, false));
+    }
   }
   c->gen += generations;
   c->model_gen = -1;
@@ -608,11 +907,33 @@ extern "C" gsgp_status gsgp_evolve(gsgp_ctx *c, int32_t generations, double *bes
     CK(cudaMemcpyAsync(h.data(), c->best_log + g0, sizeof(double2) * (size_t)generations,
                        cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
+    TRY(check_device_error(c));
     for (int k = 0; k < generations; ++k) {
       if (best_train) best_train[k] = h[k].x;
       if (best_test) best_test[k] = h[k].y;
     }
   }
+  return GSGP_OK;
+  API_END(c)
+}
+
+extern "C" gsgp_status gsgp_set_evolve_shape(gsgp_ctx *c, int32_t path, int32_t vec,
+                                             int32_t opb) {
+  API_GUARD(c)
+  if (path < 0 || path > 2) return fail(c, GSGP_E_INVALID, "path must be 0, 1 or 2");
+  const bool autotune = vec == 0 && opb == 0;
+  if (!autotune) {
+    const GenShape sh{vec, opb};
+    if (path == 0) return fail(c, GSGP_E_INVALID, "a shape needs an explicit path");
+    if (path == 1 && !persist_shape_supported(sh))
+      return fail(c, GSGP_E_INVALID, "persistent shape must have vec in {1,2}, opb in {1,2,4}");
+    if (path == 2 && !gen_shape_supported(sh))
+      return fail(c, GSGP_E_INVALID, "chained shape must have vec in {1,2,4}, opb in {2,4,8}");
+  }
+  c->forced_path = path;
+  c->forced = autotune ? GenShape{0, 0} : GenShape{vec, opb};
+  c->shape_ready = false;
+  c->graph_dirty = true;
   return GSGP_OK;
   API_END(c)
 }
@@ -642,6 +963,7 @@ static gsgp_status build_model(gsgp_ctx *c) {
   CK(cudaMemcpyAsync(&c->ancestor, c->d_anc, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   CK(cudaMemcpyAsync(&st, c->dstate, sizeof st, cudaMemcpyDeviceToHost, c->stream));
   CK(cudaStreamSynchronize(c->stream));
+  TRY(check_device_error(c));
   c->best_slot = st.best_slot;
   const size_t par = (size_t)(G & 1);
   CK(cudaMemcpyAsync(&c->best_tr, c->fit + par * m + c->best_slot, sizeof(double),
@@ -816,8 +1138,12 @@ extern "C" gsgp_status gsgp_get_info(gsgp_ctx *c, gsgp_info *out) {
   out->pop_max_genes = (1 << (c->cfg.pop_max_depth + 1)) - 1;
   out->rt_max_genes = (1 << (c->cfg.rt_max_depth + 1)) - 1;
   out->generation = c->gen;
-  out->evolve_tile_cases = gen_tile_cases(c->shape);
-  out->evolve_offspring_per_cta = c->shape.opb;
+  out->evolve_tile_cases = c->shape_ready ? gen_tile_cases(c->shape) : 0;
+  out->evolve_offspring_per_cta = c->shape_ready ? c->shape.opb : 0;
+  out->evolve_path = c->shape_ready ? c->path : 0;
+  out->evolve_grid = c->shape_ready && c->path == 1 ? c->grid : 0;
+  out->evolve_generations_per_launch =
+      c->shape_ready ? (c->path == 1 ? kPersistGenerations : 1) : 0;
   out->kernel_launches = c->launches;
   out->device_bytes = c->dev_bytes;
   return GSGP_OK;
@@ -993,6 +1319,7 @@ extern "C" void gsgp_destroy(gsgp_ctx *c) {
     dfree(c, c->t);
     dfree(c, c->d_flag);
     for (auto e : c->ev0) cudaEventDestroy(e);
+    for (auto e : c->ev_marks) cudaEventDestroy(e);
     for (auto e : c->ev1) cudaEventDestroy(e);
     cudaStreamSynchronize(c->stream);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);

@@ -84,7 +84,7 @@ struct DevState {
   int best_slot;      // best individual after the last survival
 };
 
-// Parameters of the fused generation kernel (passed by value).
+// Parameters of the generation kernels (passed by value).
 struct GenParams {
   const float *target;       // [n_pad] targets, train cases first then test
   float *pool;               // [2m][n_pad] semantic rows (population + offspring)
@@ -93,7 +93,8 @@ struct GenParams {
   double *fit;               // [2][m] training RMSE
   double *fit_te;            // [2][m] test RMSE
   double2 *partial;          // [m][tiles] per-tile (train, test) squared errors
-  unsigned *tile_count;      // [m] tiles finished per offspring (self-resetting)
+  int4 *sel;                 // [m] (parent row, offspring row, rt1, rt2) of this generation
+  float *sel_ms;             // [m] mutation step of this generation
   int4 *trace;               // [gcap][m] (parent slot, rt1, rt2, ms bits)
   double2 *best_log;         // [gcap] (train, test) RMSE of the best
   DevState *state;

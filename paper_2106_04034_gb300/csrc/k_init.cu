@@ -310,15 +310,14 @@ cudaError_t launch_fitness_finalize(const double2 *partial, int tiles, int count
 }
 
 // Generation-0 state: population slot i lives in pool row i, offspring slot
-// i will be written to row m + i; tile counters cleared; best slot found.
+// i will be written to row m + i; best slot of the initial population.
 __global__ void __launch_bounds__(kFinalThreads)
-    init_state_kernel(int m, int *perm, unsigned *tile_count, const double *fit, DevState *state) {
-  __shared__ double s_v[kFinalThreads];
+    init_state_kernel(int m, int *perm, const double *fit, DevState *state) {
+  __shared__ unsigned long long s_v[kFinalThreads];
   __shared__ int s_i[kFinalThreads];
   for (int i = threadIdx.x; i < m; i += blockDim.x) {
     perm[i] = i;
     perm[m + i] = m + i;
-    tile_count[i] = 0u;
   }
   double bv;
   int bi;
@@ -331,9 +330,9 @@ __global__ void __launch_bounds__(kFinalThreads)
   }
 }
 
-cudaError_t launch_init_state(int m, int *perm, unsigned *tile_count, const double *fit,
-                              DevState *state, cudaStream_t s) {
-  init_state_kernel<<<1, kFinalThreads, 0, s>>>(m, perm, tile_count, fit, state);
+cudaError_t launch_init_state(int m, int *perm, const double *fit, DevState *state,
+                              cudaStream_t s) {
+  init_state_kernel<<<1, kFinalThreads, 0, s>>>(m, perm, fit, state);
   return cudaGetLastError();
 }
 

@@ -25,18 +25,46 @@ cudaError_t launch_interpret(int mode, const InterpParams &p, int count, cudaStr
 cudaError_t launch_fitness_finalize(const double2 *partial, int tiles, int count, int n_train,
                                     int n_test, double *fit, double *fit_te, cudaStream_t s);
 
-cudaError_t launch_init_state(int m, int *perm, unsigned *tile_count, const double *fit,
-                              DevState *state, cudaStream_t s);
+cudaError_t launch_init_state(int m, int *perm, const double *fit, DevState *state,
+                              cudaStream_t s);
 
-// Cases per tile and offspring per CTA of the generation kernel.
+// Cases per tile and offspring per CTA of the stream kernel.
 struct GenShape {
   int vec;   // float4 chunks per thread; tile = 1024 * vec cases
   int opb;   // offspring per CTA
 };
 int gen_tile_cases(const GenShape &sh);
 bool gen_shape_supported(const GenShape &sh);
-cudaError_t launch_generation(const GenParams &p, int sigma_bf16, const GenShape &sh,
-                              cudaStream_t s);
+// One generation = select, stream, final on stream s; with pdl the launches
+// may overlap their predecessor's tail (programmatic dependent launch).
+cudaError_t launch_select(const GenParams &p, cudaStream_t s, bool pdl);
+cudaError_t launch_stream(const GenParams &p, int sigma_bf16, const GenShape &sh, cudaStream_t s,
+                          bool pdl);
+cudaError_t launch_final(const GenParams &p, cudaStream_t s, bool pdl);
+
+// Persistent cooperative generation kernel (k_persist.cu).
+// Synchronisation words of the persistent kernel, each on its own 128-byte
+// line: the sticky error word and the barrier arrival counter (zeroed before
+// every launch).
+constexpr int kSyncStride = 32;   // unsigned words per 128-byte line
+struct GridSync {
+  int err;                        // sticky: nonzero once a barrier wait gave up
+  unsigned pad0[kSyncStride - 1];
+  unsigned count;                 // barrier arrivals of the running launch
+  unsigned pad1[kSyncStride - 1];
+};
+inline size_t grid_sync_bytes(int /*grid*/) { return sizeof(GridSync); }
+struct PersistArgs {
+  GridSync *gs;
+  ulonglong2 *cta_min;   // [grid] (fitness key, index) arg-min of each CTA's offspring
+  ulonglong2 *cta_max;   // [grid] (fitness key, index) arg-max
+  int G;              // generations this launch runs
+};
+bool persist_shape_supported(const GenShape &sh);
+// Co-resident CTAs of the persistent kernel for this shape (0: no cooperative launch).
+int persist_max_grid(int sigma_bf16, const GenShape &sh);
+cudaError_t launch_persist(const GenParams &p, const PersistArgs &x, int sigma_bf16,
+                           const GenShape &sh, int grid, cudaStream_t s);
 
 cudaError_t launch_lineage(const int4 *trace, int m, int G, const DevState *state, int4 *lineage,
                            int *ancestor, cudaStream_t s);

@@ -33,45 +33,69 @@ __device__ __forceinline__ double2 warp_sum_partials(const double2 *row, int til
   return make_double2(tr, te);
 }
 
-// (value, index) order used for arg-min / arg-max: the first index wins ties.
+// Fitness values are RMSEs: >= 0 or +inf, never NaN or -0.  For such
+// doubles the IEEE bit pattern, read as an unsigned integer, orders exactly
+// like the value, so arg-min / arg-max compare 64-bit integer keys instead of
+// doubles (FP64 issue rate is a small fraction of the integer rate on this
+// GPU, and these reductions sit on the per-generation critical path).
+__device__ __forceinline__ unsigned long long fit_key(double x) {
+  return (unsigned long long)__double_as_longlong(x);
+}
+__device__ __forceinline__ double key_fit(unsigned long long k) {
+  return __longlong_as_double((long long)k);
+}
+
+// (key, index) order used for arg-min / arg-max: the first index wins ties.
 template <bool kMax>
-__device__ __forceinline__ bool arg_better(double x, int i, double bx, int bi) {
+__device__ __forceinline__ bool arg_better(unsigned long long x, int i, unsigned long long bx,
+                                           int bi) {
   if (kMax) return x > bx || (x == bx && i < bi);
   return x < bx || (x == bx && i < bi);
 }
 
-// Block-wide arg-min (kMax = false) or arg-max of v[0, n) over blockDim.x
-// threads (a power of two <= 1024).  s_v, s_i: blockDim.x scratch entries.
-// Every thread returns the result.  Loads bypass L1.
+constexpr unsigned long long kKeyAboveAll = 0x7FF0000000000001ull;   // above +inf
+constexpr unsigned long long kKeyBelowAll = 0ull;                   // = +0.0 (ties by index)
+
+// Block-wide arg-min (kMax = false) and arg-max (kMax = true) of keys, one
+// (key, index) pair per thread in and the block's result out, first index
+// on ties.  s_k, s_i: blockDim.x entries each (a power of two).
 template <bool kMax>
-__device__ void block_arg(const double *v, int n, double *s_v, int *s_i, double &out_v,
-                          int &out_i) {
-  double bx = kMax ? -CUDART_INF : CUDART_INF;
-  int bi = 0x7fffffff;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    const double x = __ldcg(v + i);
-    if (arg_better<kMax>(x, i, bx, bi)) {
-      bx = x;
-      bi = i;
-    }
-  }
-  s_v[threadIdx.x] = bx;
-  s_i[threadIdx.x] = bi;
+__device__ void block_arg_keys(unsigned long long k, int i, unsigned long long *s_k, int *s_i,
+                               unsigned long long &out_k, int &out_i) {
+  s_k[threadIdx.x] = k;
+  s_i[threadIdx.x] = i;
   __syncthreads();
   for (int w = blockDim.x >> 1; w > 0; w >>= 1) {
     if ((int)threadIdx.x < w) {
-      const double x = s_v[threadIdx.x + w];
-      const int i = s_i[threadIdx.x + w];
-      if (arg_better<kMax>(x, i, s_v[threadIdx.x], s_i[threadIdx.x])) {
-        s_v[threadIdx.x] = x;
-        s_i[threadIdx.x] = i;
+      const int o = threadIdx.x + w;
+      if (arg_better<kMax>(s_k[o], s_i[o], s_k[threadIdx.x], s_i[threadIdx.x])) {
+        s_k[threadIdx.x] = s_k[o];
+        s_i[threadIdx.x] = s_i[o];
       }
     }
     __syncthreads();
   }
-  out_v = s_v[0];
+  out_k = s_k[0];
   out_i = s_i[0];
   __syncthreads();
+}
+
+// Block-wide arg-min or arg-max of fitness values v[0, n) (loads bypass L1).
+template <bool kMax>
+__device__ void block_arg(const double *v, int n, unsigned long long *s_k, int *s_i, double &out_v,
+                          int &out_i) {
+  unsigned long long bk = kMax ? kKeyBelowAll : kKeyAboveAll;
+  int bi = 0x7fffffff;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const unsigned long long k = fit_key(__ldcg(v + i));
+    if (arg_better<kMax>(k, i, bk, bi)) {
+      bk = k;
+      bi = i;
+    }
+  }
+  unsigned long long rk;
+  block_arg_keys<kMax>(bk, bi, s_k, s_i, rk, out_i);
+  out_v = key_fit(rk);
 }
 
 }  // namespace gsgp

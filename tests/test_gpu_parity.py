@@ -323,3 +323,55 @@ def test_device_load_and_torch_allocator():
         run_d.load_device(bad, t[1], t[2], t[3])
     run_h.close()
     run_d.close()
+
+
+@pytest.mark.parametrize("path,vec,opb", [
+    (pkg.PATH_CHAINED, 1, 2), (pkg.PATH_CHAINED, 2, 4), (pkg.PATH_CHAINED, 4, 8),
+    (pkg.PATH_PERSISTENT, 1, 1), (pkg.PATH_PERSISTENT, 1, 4), (pkg.PATH_PERSISTENT, 2, 2),
+])
+def test_every_path_and_shape_gives_identical_results(path, vec, opb):
+    """The generation path (persistent cooperative kernel or chained
+    launches) and the stream shape change only the work split: the
+    per-chunk summation order is fixed, so semantics, fitness and trace are
+    bit-identical to the default run's."""
+    base, _, _ = gpu_run(MID_S)
+    base.evolve(70)          # crosses a persistent-kernel launch boundary (64)
+    other, _, _ = gpu_run(MID_S)
+    other.set_evolve_shape(path, vec, opb)
+    for n in (1, 8, 61):     # direct launches, graph replays, several chunks
+        other.evolve(n)
+    info = other.info()
+    assert info.evolve_path == path
+    assert info.evolve_tile_cases == 1024 * vec and info.evolve_offspring_per_cta == opb
+    assert np.array_equal(base.semantics(pkg.POOL_POPULATION), other.semantics(pkg.POOL_POPULATION))
+    for a, b in zip(base.fitness(), other.fitness()):
+        assert np.array_equal(a, b)
+    for a, b in zip(base.trace(), other.trace()):
+        assert np.array_equal(a, b)
+    bt1, bt2 = base.best_trace(), other.best_trace()
+    assert bt1["best_slot"] == bt2["best_slot"] and np.array_equal(bt1["coef"], bt2["coef"])
+    base.close()
+    other.close()
+
+
+@pytest.mark.parametrize("path", [pkg.PATH_PERSISTENT, pkg.PATH_CHAINED])
+def test_kernel_timing_is_reported(path):
+    run, _, _ = gpu_run(MID_S)
+    run.set_evolve_shape(path)
+    run.set_kernel_timing(True)
+    run.evolve(19)
+    t = run.kernel_times()
+    info = run.info()
+    per = info.evolve_generations_per_launch
+    assert t.shape == (-(-19 // per),) and np.all(t > 0) and np.all(t < 1000)
+    assert run.kernel_times().size == 0  # cleared
+    run.set_kernel_timing(False)
+    run.close()
+
+
+def test_default_path_is_persistent():
+    run, _, _ = gpu_run(TINY)
+    run.evolve(3)
+    info = run.info()
+    assert info.evolve_path == pkg.PATH_PERSISTENT and info.evolve_grid >= 1
+    run.close()
