@@ -290,6 +290,44 @@ gsgp_status gsgp_rng_words(uint64_t seed, uint32_t run, uint32_t gen_or_purpose,
                            uint32_t individual, int32_t n_words, uint32_t *out,
                            void *stream);
 
+/* ---- Allocation-free mutation + fitness -----------------------------------
+ *
+ * The paper has no counterpart to this call; it exists for callers that can
+ * not allocate device memory (code running while a framework captures a CUDA
+ * graph and forbids cudaMalloc, plug-ins given a fixed device budget by their
+ * host application, request paths that must not touch the allocator).  It
+ * applies one generation's geometric semantic mutation to m offspring and
+ * returns their RMSE, using only the caller's buffers plus a built-in scratch
+ * area (per-chunk partial sums) that the library keeps in a static device
+ * array of 2 MiB, held by every GPU that loads the library until exit.
+ *
+ *   offspring[i][j] = parents[parent[i]][j] + ms[i] * (sigma_r[rt1[i]][j] - sigma_r[rt2[i]][j])
+ *   rmse_train[i]   = RMSE over cases [0, n_train), rmse_test[i] over the next n_test
+ *
+ * All pointers are DEVICE memory of the current device.  Row-major matrices
+ * share the row stride ld (floats; a multiple of 4, >= n_train + n_test); the
+ * row buffers and target are 16-byte aligned and target holds ld floats.
+ * parent / rt1 / rt2 index rows of parents / sigma_r (not checked).  Work is
+ * queued on `stream` (cudaStream_t; NULL = legacy default stream); the call
+ * does not synchronise.  It calls no cudaMalloc/cudaFree and no allocating
+ * library routine.  Limit: m * ceil((n_train + n_test) / 1024) <= 131072 and
+ * m, ceil(n / 1024) <= 65535; larger sizes return GSGP_E_INVALID.
+ *
+ * The first call on a device looks up the scratch array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  Every call shares the one scratch array: calls
+ * that overlap on the GPU (for example on two streams) race and must be
+ * serialised by the caller.  Nothing in the scratch needs clearing between
+ * calls: each call writes every partial it reads.
+ *
+ * err_msg (nullable, err_cap bytes) receives a message on failure.
+ * Errors: GSGP_E_INVALID (sizes, NULL or misaligned pointers), GSGP_E_CUDA. */
+gsgp_status gsgp_mutate_noalloc(const float *parents, const float *sigma_r, int64_t ld,
+                                const float *target, int64_t n_train, int64_t n_test,
+                                const int32_t *parent, const int32_t *rt1, const int32_t *rt2,
+                                const float *ms, int32_t m, float *offspring, double *rmse_train,
+                                double *rmse_test, void *stream, char *err_msg, size_t err_cap);
+
 #ifdef __cplusplus
 }
 #endif

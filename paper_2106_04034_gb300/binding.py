@@ -101,6 +101,8 @@ _SIGS = {
     "gsgp_set_kernel_timing": (C.c_int, [P, C.c_int32]),
     "gsgp_kernel_times": (C.c_int, [P, P, C.c_int32, P]),
     "gsgp_rng_words": (C.c_int, [C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint32, C.c_int32, P, P]),
+    "gsgp_mutate_noalloc": (C.c_int, [P, P, C.c_int64, P, C.c_int64, C.c_int64, P, P, P, P,
+                                      C.c_int32, P, P, P, P, C.c_char_p, C.c_size_t]),
 }
 
 _lib = None
@@ -355,3 +357,22 @@ def rng_words(seed: int, run: int, gen_or_purpose: int, individual: int, n_words
     if st != OK:
         raise GsgpError(st, "gsgp_rng_words failed")
     return out
+
+
+def mutate_noalloc(parents, sigma_r, target, n_train, n_test, parent, rt1, rt2, ms, offspring,
+                   rmse_train, rmse_test, stream=None):
+    """gsgp_mutate_noalloc on torch CUDA tensors (row-major, common row
+    stride = parents.shape[1]); queued on `stream` (default: torch's current
+    stream).  Raises GsgpError with the library's message on failure."""
+    lib = load_library()
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream()
+    s = stream if isinstance(stream, int) else stream.cuda_stream
+    msg = C.create_string_buffer(256)
+    st = lib.gsgp_mutate_noalloc(_ptr(parents), _ptr(sigma_r), int(parents.shape[1]),
+                                 _ptr(target), n_train, n_test, _ptr(parent), _ptr(rt1),
+                                 _ptr(rt2), _ptr(ms), int(parent.shape[0]), _ptr(offspring),
+                                 _ptr(rmse_train), _ptr(rmse_test), s, msg, 256)
+    if st != OK:
+        raise GsgpError(st, msg.value.decode())
