@@ -163,8 +163,10 @@ gsgp_status gsgp_evolve(gsgp_ctx *ctx, int32_t generations, double *best_train_r
  * model: its generation-0 ancestor in P plus one coefficient per random
  * tree, obtained by walking the ancestry trace back from the best slot
  * (each mutation adds +ms to rt1's coefficient and -ms to rt2's).  The model
- * is y(x) = P_ancestor(x) + sum_k coef[k] * q(sigma(R_k(x))), where q rounds
- * to bfloat16 when sigma_dtype is BF16 and is the identity otherwise.
+ * is y(x) = P_ancestor(x) + sum_k coef[k] * q(sigma(R_k(x))), evaluated by
+ * gsgp_predict in float64; with BF16 storage, q(sigma(R_k(x))) is the value
+ * training used (R_k and the logistic in float32, rounded to bfloat16), with
+ * float32 storage q is the identity.
  * Size query: set the pointer fields to NULL to receive only the sizes.
  * All pointers are HOST buffers owned by the caller. */
 typedef struct {
@@ -264,8 +266,10 @@ gsgp_status gsgp_get_trace(gsgp_ctx *ctx, int32_t g0, int32_t count, int32_t *pa
  *     and replayed from a CUDA graph.
  * Both produce bit-identical results.  The shape of the mutation stream is
  * (vec, opb): a tile of 1024 * vec cases for opb offspring per CTA
- * (persistent: vec in {1,2}, opb in {1,2,4}; chained: vec in {1,2,4},
- * opb in {2,4,8}).  path 0 chooses the path; vec = opb = 0 (the default)
+ * (persistent: vec in {1,2} with opb in {1,2,4} streams through registers,
+ * vec in {1,2,4} with opb = 0 stages rows in shared memory with TMA bulk
+ * copies, one offspring per unit; chained: vec in {1,2,4}, opb in {2,4,8}).
+ * path 0 chooses the path; vec = opb = 0 (the default)
  * times every supported shape of the path on the first gsgp_evolve of a
  * problem layout and keeps the fastest for the process.  Results do not
  * depend on the path or the shape.  Errors: GSGP_E_INVALID. */

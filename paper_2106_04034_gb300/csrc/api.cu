@@ -579,11 +579,13 @@ static gsgp_status launch_generation(gsgp_ctx *c, const GenParams &p, cudaStream
 }
 
 // Shapes the autotuner tries: chained path (vec in {1,2,4}, opb in {2,4,8})
-// and persistent path (vec in {1,2}, opb in {1,2,4}); the choice is cached
+// and persistent path (vec in {1,2}, opb in {1,2,4} for the register stream;
+// vec in {1,2,4}, opb = 0 for the TMA-staged stream); the choice is cached
 // per problem layout for the process.
 static const GenShape kChainShapes[] = {{1, 2}, {1, 4}, {1, 8}, {2, 2}, {2, 4},
                                         {2, 8}, {4, 2}, {4, 4}, {4, 8}};
-static const GenShape kPersistShapes[] = {{1, 1}, {1, 2}, {1, 4}, {2, 1}, {2, 2}, {2, 4}};
+static const GenShape kPersistShapes[] = {{1, 1}, {1, 2}, {1, 4}, {2, 1}, {2, 2},
+                                          {2, 4}, {1, 0}, {2, 0}, {4, 0}};
 struct Tuned {
   int path;
   GenShape shape;
@@ -605,8 +607,10 @@ static int persist_grid(gsgp_ctx *c, const GenShape &sh) {
   const int max_grid = persist_max_grid(c->cfg.sigma_dtype == GSGP_SIGMA_BF16, sh);
   if (max_grid <= 0) return 0;
   const int64_t tiles = (c->n_pad + 1024 * sh.vec - 1) / (1024 * sh.vec);
-  const int64_t groups = (c->cfg.pop_size + sh.opb - 1) / sh.opb;
+  const int opb = sh.opb > 0 ? sh.opb : 1;   // the TMA variant streams one offspring per unit
+  const int64_t groups = (c->cfg.pop_size + opb - 1) / opb;
   const int64_t items = tiles * groups;
+  if (items >= ((int64_t)1 << 31)) return 0;   // item indices are 32-bit in the kernels
   const int64_t rounds = (items + max_grid - 1) / max_grid;
   const int64_t grid = (items + rounds - 1) / rounds;
   return (int)(grid < max_grid ? grid : max_grid);
@@ -921,12 +925,13 @@ extern "C" gsgp_status gsgp_set_evolve_shape(gsgp_ctx *c, int32_t path, int32_t 
                                              int32_t opb) {
   API_GUARD(c)
   if (path < 0 || path > 2) return fail(c, GSGP_E_INVALID, "path must be 0, 1 or 2");
-  const bool autotune = vec == 0 && opb == 0;
+  const bool autotune = vec == 0 && opb == 0;   // (vec, 0) with vec > 0 is the TMA variant
   if (!autotune) {
     const GenShape sh{vec, opb};
     if (path == 0) return fail(c, GSGP_E_INVALID, "a shape needs an explicit path");
     if (path == 1 && !persist_shape_supported(sh))
-      return fail(c, GSGP_E_INVALID, "persistent shape must have vec in {1,2}, opb in {1,2,4}");
+      return fail(c, GSGP_E_INVALID,
+                  "persistent shape: vec in {1,2} with opb in {1,2,4}, or vec in {1,2,4} with opb 0");
     if (path == 2 && !gen_shape_supported(sh))
       return fail(c, GSGP_E_INVALID, "chained shape must have vec in {1,2,4}, opb in {2,4,8}");
   }

@@ -21,11 +21,11 @@
 // the parents chosen by several offspring are then served from L2 while
 // parent and offspring rows stream through HBM once.  Each thread handles
 // 4 * VEC cases with float4 accesses; per offspring and 1024-case chunk the
-// squared errors are summed in float per thread (4 cases), reduced with warp
-// shuffles and then in double over the 8 warps, and written as one (train,
-// test) partial (no atomics).  The chunking and summation order are the same
-// for every shape and match the interpreter's, so fitness values, and hence
-// every selection decision, do not depend on the shape the autotuner picks.
+// squared errors are summed in the canonical chunk order (subblock_sum,
+// chunk_total) and written as one (train, test) partial (no atomics).  The chunking and
+// summation order are the same for every shape and kernel, so fitness
+// values, and hence every selection decision, do not depend on the shape the
+// autotuner picks.
 //
 // Data written by an earlier launch of the chain (rows, draws, fitness, the
 // slot-to-row map, partial sums) is read with ld.global.cg so that no stale
@@ -71,7 +71,7 @@ template <typename SigT, int VEC, int OPB>
 __global__ void __launch_bounds__(kGenThreads) stream_kernel(const GenParams p) {
   constexpr int W = kGenThreads * 4 * VEC;
   constexpr int NW = kGenThreads / 32;
-  __shared__ float s_red[OPB][VEC][NW][2];
+  __shared__ float2 s_sub[OPB][VEC][NW];   // sub-block totals per offspring and chunk
   griddep_wait();
   griddep_launch();
 
@@ -99,32 +99,20 @@ __global__ void __launch_bounds__(kGenThreads) stream_kernel(const GenParams p) 
     }
 #pragma unroll
     for (int v = 0; v < VEC; ++v) {
-      // chunk v = cases [base + 1024 v, base + 1024 (v + 1)); thread tid owns
-      // 4 consecutive cases of it, exactly as in every other shape, so the
-      // per-chunk sums below do not depend on the shape
+      // chunk v = cases [base + 1024 v, base + 1024 (v + 1)): sub-block = warp,
+      // 4 consecutive cases per lane, as in every other kernel
       const int64_t j0 = base + v * 1024 + tid * 4;
       float str = 0.f, ste = 0.f;
       if (j0 < p.n_pad) mutate4<SigT>(p, src, dst, ra, rb, j0, step, str, ste);
-      warp_sum2(str, ste);
-      if (lane == 0) {
-        s_red[k][v][warp][0] = str;
-        s_red[k][v][warp][1] = ste;
-      }
+      const float2 sub = subblock_sum(str, ste);
+      if (lane == 0) s_sub[k][v][warp] = sub;
     }
   }
   __syncthreads();
-  // one (train, test) partial per offspring and 1024-case chunk
-  const int chunk0 = tile * VEC;
   for (int e = tid; e < cnt * VEC; e += kGenThreads) {
     const int k = e / VEC, v = e - k * VEC;
-    if (chunk0 + v >= p.tiles) continue;
-    double tr = 0.0, te = 0.0;
-#pragma unroll
-    for (int w = 0; w < NW; ++w) {
-      tr += (double)s_red[k][v][w][0];
-      te += (double)s_red[k][v][w][1];
-    }
-    p.partial[(size_t)(i0 + k) * p.tiles + chunk0 + v] = make_double2(tr, te);
+    if (tile * VEC + v < p.tiles)
+      p.partial[(size_t)(i0 + k) * p.tiles + tile * VEC + v] = chunk_total(s_sub[k][v]);
   }
 }
 

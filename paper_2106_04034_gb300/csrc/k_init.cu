@@ -3,6 +3,7 @@
 // case) and ComputeFitness of the initial population, plus data staging.
 #include "kernels.cuh"
 #include "reduce.cuh"
+#include "stream.cuh"
 
 namespace gsgp {
 
@@ -144,7 +145,8 @@ cudaError_t launch_nonfinite_check(const float *v, int64_t n, unsigned *flag, cu
 // paper's rule; generated programs never trigger it).  Protected division
 // returns 1 when |b| < eps.  Random trees are wrapped by the logistic
 // function (Sec. 2) and stored as float or bf16.  For the population the
-// CTA also reduces the squared errors of its tile (train and test cases).
+// CTA also reduces the squared errors of its tile (train and test cases) in
+// the canonical chunk order (subblock_sum, chunk_total).
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ float apply_op(int op, float a, float b, float eps) {
   switch (op) {
@@ -166,7 +168,7 @@ __global__ void __launch_bounds__(kInterpThreads) interpret_kernel(InterpParams 
   float4 *s_stack = reinterpret_cast<float4 *>(smem_raw);
   int *s_gene = reinterpret_cast<int *>(s_stack + (size_t)p.stack_slots * kInterpThreads);
   float *s_const = reinterpret_cast<float *>(s_gene + p.K);
-  __shared__ float s_red[kInterpThreads / 32][2];
+  __shared__ float2 s_sub[kInterpThreads / 32];   // sub-block (warp) totals
 
   const int prog = blockIdx.x;
   const int tile = blockIdx.y;
@@ -224,24 +226,10 @@ __global__ void __launch_bounds__(kInterpThreads) interpret_kernel(InterpParams 
           ste += d * d;
       }
     }
-#pragma unroll
-    for (int o = 16; o; o >>= 1) {
-      str += __shfl_xor_sync(0xffffffffu, str, o);
-      ste += __shfl_xor_sync(0xffffffffu, ste, o);
-    }
-    if ((tid & 31) == 0) {
-      s_red[tid >> 5][0] = str;
-      s_red[tid >> 5][1] = ste;
-    }
+    const float2 sub = subblock_sum(str, ste);
+    if ((tid & 31) == 0) s_sub[tid >> 5] = sub;
     __syncthreads();
-    if (tid == 0) {
-      double a = 0.0, b = 0.0;
-      for (int w = 0; w < kInterpThreads / 32; ++w) {
-        a += (double)s_red[w][0];
-        b += (double)s_red[w][1];
-      }
-      p.partial[(size_t)prog * p.tiles + tile] = make_double2(a, b);
-    }
+    if (tid == 0) p.partial[(size_t)prog * p.tiles + tile] = chunk_total(s_sub);
   } else if (valid) {
     const float4 sg = make_float4(logistic(tos.x), logistic(tos.y), logistic(tos.z),
                                   logistic(tos.w));

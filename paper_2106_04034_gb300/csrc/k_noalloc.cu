@@ -10,10 +10,9 @@
 // scratch, the per-chunk squared-error partial sums, lives in the
 // file-scope device array below instead of a cudaMalloc'd buffer.
 //
-// The per-chunk summation order is the same as in the library's generation
-// kernels (4 cases per thread in float, warp butterfly, 8 warps in double,
-// chunks in a fixed lane-strided order), so the results equal the ones the
-// library computes for the same offspring.
+// The per-chunk summation order is the library's canonical one (chunk_total)
+// and chunks are added in the same fixed lane-strided order, so the results
+// equal the ones the library computes for the same offspring.
 #include <mutex>
 
 #include "gsgp.h"
@@ -43,8 +42,7 @@ struct NoAllocArgs {
 // One CTA = one offspring x one 1024-case chunk.
 __global__ void __launch_bounds__(kGenThreads) noalloc_mutate_kernel(const GenParams p,
                                                                      const NoAllocArgs a) {
-  constexpr int NW = kGenThreads / 32;
-  __shared__ float s_red[NW][2];
+  __shared__ float2 s_sub[kGenThreads / 32];   // sub-block (warp) totals
   const int chunk = blockIdx.x;
   const int i = blockIdx.y;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -55,20 +53,10 @@ __global__ void __launch_bounds__(kGenThreads) noalloc_mutate_kernel(const GenPa
   const int64_t j0 = (int64_t)chunk * 1024 + tid * 4;
   float str = 0.f, ste = 0.f;
   if (j0 < p.n_cases) mutate4<float>(p, src, dst, ra, rb, j0, a.ms[i], str, ste);
-  warp_sum2(str, ste);
-  if (lane == 0) {
-    s_red[warp][0] = str;
-    s_red[warp][1] = ste;
-  }
+  const float2 sub = subblock_sum(str, ste);
+  if (lane == 0) s_sub[warp] = sub;
   __syncthreads();
-  if (tid == 0) {
-    double tr = 0.0, te = 0.0;
-    for (int w = 0; w < NW; ++w) {
-      tr += (double)s_red[w][0];
-      te += (double)s_red[w][1];
-    }
-    a.partial[(size_t)i * a.chunks + chunk] = make_double2(tr, te);
-  }
+  if (tid == 0) a.partial[(size_t)i * a.chunks + chunk] = chunk_total(s_sub);
 }
 
 // One warp per offspring: fixed-order sum of its chunk partials, RMSE.

@@ -58,8 +58,44 @@ __device__ double eval_program64(const int *__restrict__ genes, const float *__r
   return sp ? st[sp - 1] : 0.0;
 }
 
-// y(x) = ancestor(x) + sum_k coef_k * q(sigma(R_k(x))) in float64; q rounds
-// to bf16 (through float, nearest-even) when sigma was stored as bf16.
+// Float32 evaluation of one program on case j with the interpreter's
+// arithmetic (one rounding per operation, protected division on the float
+// divisor), so that sigma of a random tree comes out bit-identical to the
+// value the interpreter stored during initialisation.
+__device__ float eval_program32(const int *__restrict__ genes, const float *__restrict__ consts,
+                                int len, const float *__restrict__ X, int64_t n_pad, int64_t j,
+                                float eps) {
+  float st[kMaxDepth + 2];
+  int sp = 0;
+  for (int k = 0; k < len; ++k) {
+    const int g = genes[k];
+    const int op = g & 0xFF;
+    if (op == kOpVar) {
+      if (sp < kMaxDepth + 2) st[sp++] = X[(int64_t)(g >> 8) * n_pad + j];
+    } else if (op == kOpConst) {
+      if (sp < kMaxDepth + 2) st[sp++] = consts[k];
+    } else if (sp >= 2) {
+      const float b = st[sp - 1];
+      const float a = st[sp - 2];
+      float r;
+      switch (op) {
+        case kOpAdd: r = a + b; break;
+        case kOpSub: r = a - b; break;
+        case kOpMul: r = a * b; break;
+        default: r = fabsf(b) < eps ? 1.0f : a / b; break;
+      }
+      st[sp - 2] = r;
+      --sp;
+    }
+  }
+  return sp ? st[sp - 1] : 0.0f;
+}
+
+// y(x) = ancestor(x) + sum_k coef_k * q(sigma(R_k(x))) in float64.  With
+// float32 storage q is the identity and the programs are evaluated in
+// float64.  With bf16 storage q(sigma(R_k(x))) is the value training used:
+// R_k evaluated in float32, the logistic in float32, rounded to bf16
+// (nearest-even), so the rebuilt model reproduces the training semantics.
 __global__ void __launch_bounds__(128) predict_kernel(const PredictParams p) {
   const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= p.n) return;
@@ -67,10 +103,17 @@ __global__ void __launch_bounds__(128) predict_kernel(const PredictParams p) {
   double y = eval_program64(p.anc_genes, p.anc_consts, p.anc_len, p.X, p.n_pad, j, eps);
   for (int q = 0; q < p.nk; ++q) {
     const int k = p.terms[q];
-    const double v = eval_program64(p.rt_genes + (size_t)k * p.Kr, p.rt_consts + (size_t)k * p.Kr,
-                                    p.rt_len[k], p.X, p.n_pad, j, eps);
-    double sg = 1.0 / (1.0 + exp(-v));
-    if (p.sigma_bf16) sg = (double)__bfloat162float(__float2bfloat16_rn(__double2float_rn(sg)));
+    double sg;
+    if (p.sigma_bf16) {
+      const float v = eval_program32(p.rt_genes + (size_t)k * p.Kr, p.rt_consts + (size_t)k * p.Kr,
+                                     p.rt_len[k], p.X, p.n_pad, j, p.protect_eps);
+      sg = (double)__bfloat162float(__float2bfloat16_rn(1.0f / (1.0f + expf(-v))));
+    } else {
+      const double v = eval_program64(p.rt_genes + (size_t)k * p.Kr,
+                                      p.rt_consts + (size_t)k * p.Kr, p.rt_len[k], p.X, p.n_pad, j,
+                                      eps);
+      sg = 1.0 / (1.0 + exp(-v));
+    }
     y += p.coef[q] * sg;
   }
   p.y[j] = y;

@@ -121,4 +121,33 @@ __device__ __forceinline__ void warp_sum2(float &a, float &b) {
   }
 }
 
+// Canonical (train, test) squared-error sum of one 1024-case chunk.  The
+// chunk is 8 sub-blocks of 128 cases, one per warp; lane l of sub-block k
+// holds the float sum of its 4 cases (k * 128 + 4 l ... + 3, added in case
+// order from 0).  A warp butterfly (xor 16, 8, 4, 2, 1) gives the sub-block
+// total; every lane ends with the same value because each step adds the same
+// two numbers on both partner lanes.  The 8 sub-block totals are then added
+// in sub-block order (float, from 0) and the result is widened to double
+// once.  Every kernel that computes squared errors (interpreter, chained and
+// persistent generation kernels, allocation-free entry point) produces its
+// chunk sums this way, so fitness values do not depend on which kernel or
+// which work split computed them, and the float64 work per chunk is one
+// conversion (float64 issue is scarce on this GPU).
+__device__ __forceinline__ float2 subblock_sum(float lane_tr, float lane_te) {
+  warp_sum2(lane_tr, lane_te);
+  return make_float2(lane_tr, lane_te);
+}
+
+// Chunk sum from its 8 sub-block totals sub[0..7].
+__device__ __forceinline__ double2 chunk_total(const float2 *sub) {
+  float a = 0.f, b = 0.f;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    const float2 v = sub[k];
+    a += v.x;
+    b += v.y;
+  }
+  return make_double2((double)a, (double)b);
+}
+
 }  // namespace gsgp

@@ -328,6 +328,7 @@ def test_device_load_and_torch_allocator():
 @pytest.mark.parametrize("path,vec,opb", [
     (pkg.PATH_CHAINED, 1, 2), (pkg.PATH_CHAINED, 2, 4), (pkg.PATH_CHAINED, 4, 8),
     (pkg.PATH_PERSISTENT, 1, 1), (pkg.PATH_PERSISTENT, 1, 4), (pkg.PATH_PERSISTENT, 2, 2),
+    (pkg.PATH_PERSISTENT, 1, 0), (pkg.PATH_PERSISTENT, 2, 0), (pkg.PATH_PERSISTENT, 4, 0),
 ])
 def test_every_path_and_shape_gives_identical_results(path, vec, opb):
     """The generation path (persistent cooperative kernel or chained
@@ -343,6 +344,8 @@ def test_every_path_and_shape_gives_identical_results(path, vec, opb):
     info = other.info()
     assert info.evolve_path == path
     assert info.evolve_tile_cases == 1024 * vec and info.evolve_offspring_per_cta == opb
+    if opb == 0:          # TMA-staged stream: 9 warps, one CTA per SM
+        assert 1 <= info.evolve_grid <= 2 * 152
     assert np.array_equal(base.semantics(pkg.POOL_POPULATION), other.semantics(pkg.POOL_POPULATION))
     for a, b in zip(base.fitness(), other.fitness()):
         assert np.array_equal(a, b)
