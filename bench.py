@@ -169,6 +169,9 @@ def run_ours(args, rank, world, local_rank):
         sigma_dtype=pkg.SIGMA_BF16 if w.sigma_bf16 else pkg.SIGMA_F32)
     cfg.stream = stream.cuda_stream
     run = pkg.Run(cfg)
+    if args.shape:
+        vec, opb = (int(v) for v in args.shape.split(","))
+        run.set_evolve_shape(pkg.PATH_PERSISTENT, vec, opb)
     y_pred = torch.zeros(w.n_test, dtype=torch.float64, device="cuda")
 
     def step():
@@ -289,6 +292,186 @@ def run_ours(args, rank, world, local_rank):
     return line, w
 
 
+def make_config(pkg, w: W.Workload, stream):
+    cfg = pkg.default_config(
+        seed=w.seed, run=w.run, pop_size=w.pop_size, n_random_trees=w.n_random_trees,
+        pop_min_depth=w.pop_min_depth, pop_max_depth=w.pop_max_depth,
+        rt_min_depth=w.rt_min_depth, rt_max_depth=w.rt_max_depth, ms=w.ms,
+        tournament_size=w.tournament_size, const_lo=w.const_lo, const_hi=w.const_hi,
+        protect_eps=w.protect_eps,
+        sigma_dtype=pkg.SIGMA_BF16 if w.sigma_bf16 else pkg.SIGMA_F32)
+    cfg.stream = stream.cuda_stream
+    return cfg
+
+
+BATCH_RUNS = 48
+
+
+def run_batched(args, rank, world, local_rank):
+    """48 independent runs of uneven shapes: one step = every run staged,
+    initialised, evolved G generations by the batched kernel (one
+    cooperative launch per 64 generations of all runs), its best model
+    rebuilt and applied to its test cases.  The same runs executed one after
+    another through the single-run path are timed alongside."""
+    import torch
+
+    import paper_2106_04034_gb300 as pkg
+    from paper_2106_04034_gb300.build import build_library
+
+    torch.cuda.set_device(local_rank)
+    build_library()
+    G = args.generations or 500
+    nruns = args.batch_runs
+    ws = [w.replace(run=w.run + 1000 * rank)
+          for w in W.batched_runs(nruns, generations=G, max_train=args.max_train or None)]
+    datas = [W.make_data(w) for w in ws]
+    devs = [[torch.from_numpy(a).cuda() for a in d] for d in datas]
+    stream = torch.cuda.current_stream()
+    runs = [pkg.Run(make_config(pkg, w, stream)) for w in ws]
+    for r, d in zip(runs, devs):
+        r.load_device(*d)
+        r.init()
+    batch = pkg.Batch(runs)
+    if args.shape:
+        batch.set_shape(*(int(v) for v in args.shape.split(",")))
+    y_pred = [torch.zeros(max(w.n_test, 1), dtype=torch.float64, device="cuda") for w in ws]
+
+    def finish():
+        for r, d, y in zip(runs, devs, y_pred):
+            r.best_trace()
+            r.predict_device(d[2], y)
+
+    def step():
+        for r, d in zip(runs, devs):
+            r.load_device(*d)
+            r.init()
+        batch.evolve(G, log=False)
+        finish()
+
+    def step_sequential():
+        for r, d in zip(runs, devs):
+            r.load_device(*d)
+            r.init()
+            r.evolve(G, log=False)
+        finish()
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    def timed(fn, steps):
+        barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            fn()
+        e1.record(stream)
+        barrier()
+        ms = e0.elapsed_time(e1)
+        if world > 1:
+            t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms / steps
+
+    for _ in range(args.warmup):
+        step()
+    batch.set_kernel_timing(True)
+    launches0 = batch.info().kernel_launches + sum(r.info().kernel_launches for r in runs)
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    ms_step = timed(step, args.steps)
+    clock = clocks.stop()
+    kms = batch.kernel_times(1 << 20)
+    batch.set_kernel_timing(False)
+    launches = batch.info().kernel_launches + sum(r.info().kernel_launches for r in runs) - launches0
+    updates = float(sum(w.pop_size * w.n_cases for w in ws)) * G
+    value = updates * world / (ms_step / 1e3)
+
+    # roofline of the batched kernel: algorithmic bytes of every run's
+    # generations (distinct parents and random trees read once, offspring
+    # written once, targets once) per launch of up to 64 generations
+    info = batch.info()
+    per = info.generations_per_launch
+    ub = sum(unique_bytes_per_generation(r, w, 2 if w.sigma_bf16 else 4)
+             for r, w in zip(runs, ws))
+    bounds = list(range(0, G, per)) + [G]
+    per_launch = np.array([ub[a:b].sum() for a, b in zip(bounds[:-1], bounds[1:])])
+    assert kms.size == per_launch.size * args.steps, (kms.size, per_launch.size)
+    total_bytes = float(per_launch.sum()) * args.steps
+    achieved = total_bytes / (float(kms.sum()) / 1e3) / 1e9
+    peak, peak_kind = measured_peak_gbs()
+
+    # the same runs one after another through the single-run path
+    step_sequential()                       # autotunes each run's layout once
+    seq_steps = max(1, min(args.steps, 2))
+    ms_seq = timed(step_sequential, seq_steps)
+    value_seq = updates * world / (ms_seq / 1e3)
+
+    # end to end through host buffers
+    def step_host():
+        for r, d in zip(runs, datas):
+            r.load(*d)
+            r.init()
+        batch.evolve(G, log=False)
+        return [r.predict(d[2]) for r, d in zip(runs, datas)]
+
+    step_host()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step_host()
+    barrier()
+    e2e_s = (time.perf_counter() - t0) / args.steps
+    if world > 1:
+        t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    h2d = sum(sum(a.nbytes for a in d) + d[2].nbytes for d in datas)
+    d2h = sum(w.n_test * 8 for w in ws)
+    batch.close()
+    for r in runs:
+        r.close()
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"batched: {nruns} runs, n_train log-uniform 1e3-2e5"
+                               + (f" capped at {args.max_train}" if args.max_train else "")
+                               + f", n_test = n_train/4, l 5-100, m 256-2048, r 256-1024, "
+                               f"depth 2-6, G={G}",
+                   "runs": nruns, "generations": G,
+                   "updates_per_generation": updates / G,
+                   "parallelism": f"replicas x{world}",
+                   "l2": "working set larger than L2 (%.1f GB of semantic rows)"
+                         % (sum((2 * w.pop_size + w.n_random_trees) * w.n_cases * 4
+                                for w in ws) / 1e9),
+                   "step": "per run load_device + init; batched evolve(G); per run "
+                           "best_trace + predict(test)"},
+        "sequential": {"value": value_seq, "unit": UNIT, "ms_per_step": ms_seq,
+                       "steps": seq_steps,
+                       "what": "the same runs one after another through gsgp_evolve"},
+        "roofline": {"kernel": "batch_kernel", "bound": "hbm", "achieved": achieved,
+                     "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "algorithmic_bytes_per_launch": total_bytes / kms.size,
+                     "avg_launch_ms": float(kms.mean()), "launches_timed": int(kms.size),
+                     "generations_per_launch": per,
+                     "shape": {"tile_cases": info.tile_cases,
+                               "offspring_per_cta": info.offspring_per_cta,
+                               "grid": info.grid, "graph": bool(info.graph)}},
+        "e2e": {"value": updates * world / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                "d2h_bytes_per_step": int(d2h)},
+        "gpu_launches": int(launches),
+        "clocks": clock,
+    }
+    return line, ws
+
+
 def cpu_baseline(w: W.Workload, target_s: float = 12.0, max_gens: int = 200):
     """The float64 oracle, as it stands, on the host cores: generations of the
     same workload until about target_s seconds of evolution were timed."""
@@ -318,7 +501,10 @@ def run_reference(args, rank):
     """The CPU oracle as the reference arm: each step a bounded sample of the
     same workload (a few generations of the oracle after an untimed init)."""
     from oracle import gsgp as og
-    w = W.WORKLOADS[args.workload]
+    if args.workload == "batched":   # the smallest run of the batch
+        w = min(W.batched_runs(args.batch_runs), key=lambda x: x.pop_size * x.n_cases)
+    else:
+        w = W.WORKLOADS[args.workload]
     if args.generations:
         w = w.replace(generations=args.generations)
     p = og.Params(seed=w.seed, run=w.run, pop_size=w.pop_size,
@@ -361,10 +547,16 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="mid", choices=sorted(W.WORKLOADS))
+    ap.add_argument("--workload", default="mid", choices=sorted(W.WORKLOADS) + ["batched"])
     ap.add_argument("--generations", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-gens-per-step", type=int, default=3)
+    ap.add_argument("--shape", default="",
+                    help="vec,opb of the mutation stream instead of autotuning (e.g. 2,4)")
+    ap.add_argument("--batch-runs", type=int, default=BATCH_RUNS,
+                    help="runs of the batched workload")
+    ap.add_argument("--max-train", type=int, default=0,
+                    help="cap on n_train of the batched workload's runs (0: none)")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -380,7 +572,12 @@ def main():
         import torch
         torch.cuda.set_device(local_rank)
         torch.distributed.init_process_group("nccl")
-    line, w = run_ours(args, rank, world, local_rank)
+    if args.workload == "batched":
+        line, ws = run_batched(args, rank, world, local_rank)
+        # the oracle on the smallest run of the batch
+        w = min(ws, key=lambda x: x.pop_size * x.n_cases).replace(run=0)
+    else:
+        line, w = run_ours(args, rank, world, local_rank)
     if rank == 0:
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(w.replace(run=0))

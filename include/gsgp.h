@@ -270,9 +270,10 @@ gsgp_status gsgp_get_trace(gsgp_ctx *ctx, int32_t g0, int32_t count, int32_t *pa
  * vec in {1,2,4} with opb = 0 stages rows in shared memory with TMA bulk
  * copies, one offspring per unit; chained: vec in {1,2,4}, opb in {2,4,8}).
  * path 0 chooses the path; vec = opb = 0 (the default)
- * times every supported shape of the path on the first gsgp_evolve of a
- * problem layout and keeps the fastest for the process.  Results do not
- * depend on the path or the shape.  Errors: GSGP_E_INVALID. */
+ * times every register-stream shape of the path (one generation each) on
+ * the first gsgp_evolve of a problem layout and keeps the fastest for the
+ * process; the TMA-staged shapes run only when set explicitly.  Results do
+ * not depend on the path or the shape.  Errors: GSGP_E_INVALID. */
 enum { GSGP_PATH_AUTO = 0, GSGP_PATH_PERSISTENT = 1, GSGP_PATH_CHAINED = 2 };
 gsgp_status gsgp_set_evolve_shape(gsgp_ctx *ctx, int32_t path, int32_t vec, int32_t opb);
 
@@ -293,6 +294,80 @@ gsgp_status gsgp_kernel_times(gsgp_ctx *ctx, float *ms, int32_t cap, int32_t *n_
 gsgp_status gsgp_rng_words(uint64_t seed, uint32_t run, uint32_t gen_or_purpose,
                            uint32_t individual, int32_t n_words, uint32_t *out,
                            void *stream);
+
+/* ---- Batched runs ----------------------------------------------------------
+ *
+ * Several independent runs, each its own context (data, sizes, parameters,
+ * random trees, state), evolved together.  The paper evolves one run at a
+ * time and repeats runs from a host loop (Sec. 3.3); a batch advances all of
+ * its runs by the same number of generations with one persistent cooperative
+ * kernel launch per up to 64 generations (captured once in a CUDA graph and
+ * replayed) over the flattened work of all runs: selection of every run's
+ * offspring, the mutation stream over every run's case tiles, every
+ * offspring's RMSE, then survival per run.  A run evolved in a batch is
+ * bit-identical to the same run evolved alone with gsgp_evolve, and every
+ * single-run call (evolve, best_trace, predict, get_*) keeps working on it
+ * between batch calls.
+ *
+ * The batch does not own its runs: they must outlive it.  A run may be
+ * re-loaded or re-initialised between batch calls (the batch reads each
+ * run's sizes and buffers at every gsgp_batch_evolve), but must then be
+ * initialised again before the next one. */
+typedef struct gsgp_batch gsgp_batch;
+
+/* Group `count` (1 .. 1024) distinct initialised runs on one device, all
+ * with the same sigma_dtype.  The batch's device work is ordered on
+ * runs[0]'s config.stream; each gsgp_batch_evolve first waits for the work
+ * already queued on every run's stream and then makes every run's stream
+ * wait for the batch.  Allocates a few bytes of device memory per run.
+ * Errors: GSGP_E_INVALID (NULL, count out of range, a run given twice,
+ * mixed devices or sigma dtypes), GSGP_E_STATE (a run not initialised),
+ * GSGP_E_OOM, GSGP_E_CUDA. */
+gsgp_status gsgp_batch_create(gsgp_ctx *const *runs, int32_t count, gsgp_batch **out);
+
+/* Advance every run of the batch by `generations` generations, each from its
+ * own current generation.  best_train_rmse / best_test_rmse (nullable HOST
+ * arrays of count * generations doubles, run-major) receive per run what
+ * gsgp_evolve would return; when both are NULL the call does not
+ * synchronise.  The first call times every supported shape on one
+ * generation of the whole batch (state restored) unless a shape was set.
+ * Errors: GSGP_E_STATE (a run not initialised), GSGP_E_INVALID, GSGP_E_OOM,
+ * GSGP_E_CUDA, GSGP_E_TIMEOUT (then every run must be re-initialised). */
+gsgp_status gsgp_batch_evolve(gsgp_batch *batch, int32_t generations, double *best_train_rmse,
+                              double *best_test_rmse);
+
+/* Shape of the batch's mutation stream: tiles of 1024 * vec cases for opb
+ * offspring per CTA, vec in {1, 2}, opb in {1, 2, 4}; (0, 0), the default,
+ * autotunes.  Results do not depend on the shape.  Errors: GSGP_E_INVALID. */
+gsgp_status gsgp_batch_set_shape(gsgp_batch *batch, int32_t vec, int32_t opb);
+
+/* Kernel timing of the batch, as gsgp_set_kernel_timing / gsgp_kernel_times:
+ * one duration per launch (up to 64 generations of every run). */
+gsgp_status gsgp_batch_set_kernel_timing(gsgp_batch *batch, int32_t enabled);
+gsgp_status gsgp_batch_kernel_times(gsgp_batch *batch, float *ms, int32_t cap, int32_t *n_out);
+
+typedef struct {
+  uint32_t struct_size;            /* in: sizeof(gsgp_batch_info) */
+  int32_t runs;
+  int32_t tile_cases;              /* 1024 * vec (0 before the first evolve chose a shape) */
+  int32_t offspring_per_cta;       /* opb */
+  int32_t grid;                    /* CTAs of the batched kernel */
+  int32_t generations_per_launch;
+  int32_t graph;                   /* 1: full launches replay a captured CUDA graph */
+  int64_t offspring;               /* sum over runs of m */
+  int64_t updates_per_generation;  /* sum over runs of m * n_cases */
+  int64_t items_per_generation;    /* stream items of all runs in the chosen shape */
+  int64_t kernel_launches;         /* batched-kernel launches since create */
+} gsgp_batch_info;
+
+gsgp_status gsgp_batch_get_info(gsgp_batch *batch, gsgp_batch_info *out);
+
+/* Last error message of the batch ("" if none). */
+const char *gsgp_batch_last_error(const gsgp_batch *batch);
+
+/* Release the batch (NULL is ignored); its runs are not touched.
+ * Synchronises the batch's stream. */
+void gsgp_batch_destroy(gsgp_batch *batch);
 
 /* ---- Allocation-free mutation + fitness -----------------------------------
  *

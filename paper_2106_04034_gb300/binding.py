@@ -78,6 +78,16 @@ class Info(C.Structure):
     ]
 
 
+class BatchInfo(C.Structure):
+    _fields_ = [
+        ("struct_size", C.c_uint32), ("runs", C.c_int32), ("tile_cases", C.c_int32),
+        ("offspring_per_cta", C.c_int32), ("grid", C.c_int32),
+        ("generations_per_launch", C.c_int32), ("graph", C.c_int32),
+        ("offspring", C.c_int64), ("updates_per_generation", C.c_int64),
+        ("items_per_generation", C.c_int64), ("kernel_launches", C.c_int64),
+    ]
+
+
 P = C.c_void_p
 _SIGS = {
     "gsgp_config_default": (None, [C.POINTER(Config)]),
@@ -103,6 +113,14 @@ _SIGS = {
     "gsgp_rng_words": (C.c_int, [C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint32, C.c_int32, P, P]),
     "gsgp_mutate_noalloc": (C.c_int, [P, P, C.c_int64, P, C.c_int64, C.c_int64, P, P, P, P,
                                       C.c_int32, P, P, P, P, C.c_char_p, C.c_size_t]),
+    "gsgp_batch_create": (C.c_int, [P, C.c_int32, C.POINTER(P)]),
+    "gsgp_batch_evolve": (C.c_int, [P, C.c_int32, P, P]),
+    "gsgp_batch_set_shape": (C.c_int, [P, C.c_int32, C.c_int32]),
+    "gsgp_batch_set_kernel_timing": (C.c_int, [P, C.c_int32]),
+    "gsgp_batch_kernel_times": (C.c_int, [P, P, C.c_int32, P]),
+    "gsgp_batch_get_info": (C.c_int, [P, C.POINTER(BatchInfo)]),
+    "gsgp_batch_last_error": (C.c_char_p, [P]),
+    "gsgp_batch_destroy": (None, [P]),
 }
 
 _lib = None
@@ -345,6 +363,71 @@ class Run:
         n = C.c_int32(0)
         self._check(self.lib.gsgp_kernel_times(self.ctx, _ptr(out), cap, C.byref(n)))
         return out[:n.value].copy()
+
+
+class Batch:
+    """Independent runs evolved together (one gsgp_batch).  The runs must
+    be initialised and must outlive the batch; they stay usable as Run
+    objects (best_trace, predict, semantics, ...)."""
+
+    def __init__(self, runs):
+        self.lib = load_library()
+        self.runs = list(runs)
+        arr = (P * len(self.runs))(*[r.ctx.value for r in self.runs])
+        self.handle = P()
+        st = self.lib.gsgp_batch_create(arr, len(self.runs), C.byref(self.handle))
+        if st != OK:
+            raise GsgpError(st, "gsgp_batch_create failed")
+
+    def _check(self, st):
+        if st != OK:
+            raise GsgpError(st, self.lib.gsgp_batch_last_error(self.handle).decode())
+
+    def close(self):
+        if self.handle:
+            self.lib.gsgp_batch_destroy(self.handle)
+            self.handle = P()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def evolve(self, generations: int, log: bool = True):
+        """Advance every run; with log, (train, test) arrays of shape
+        (runs, generations) of the best RMSE per generation."""
+        if not log:
+            self._check(self.lib.gsgp_batch_evolve(self.handle, generations, None, None))
+            return None
+        tr = np.zeros((len(self.runs), generations), dtype=np.float64)
+        te = np.zeros((len(self.runs), generations), dtype=np.float64)
+        self._check(self.lib.gsgp_batch_evolve(self.handle, generations, _ptr(tr), _ptr(te)))
+        return tr, te
+
+    def set_shape(self, vec: int = 0, opb: int = 0):
+        self._check(self.lib.gsgp_batch_set_shape(self.handle, vec, opb))
+
+    def set_kernel_timing(self, enabled: bool):
+        self._check(self.lib.gsgp_batch_set_kernel_timing(self.handle, int(enabled)))
+
+    def kernel_times(self, cap: int = 1 << 16) -> np.ndarray:
+        out = np.zeros(cap, np.float32)
+        n = C.c_int32(0)
+        self._check(self.lib.gsgp_batch_kernel_times(self.handle, _ptr(out), cap, C.byref(n)))
+        return out[:n.value].copy()
+
+    def info(self) -> BatchInfo:
+        i = BatchInfo()
+        i.struct_size = C.sizeof(BatchInfo)
+        self._check(self.lib.gsgp_batch_get_info(self.handle, C.byref(i)))
+        return i
 
 
 def rng_words(seed: int, run: int, gen_or_purpose: int, individual: int, n_words: int,

@@ -12,96 +12,12 @@
 #include <unordered_map>
 #include <vector>
 
-#include "gsgp.h"
-#include "kernels.cuh"
+#include "ctx.h"
 
 using namespace gsgp;
 
-struct gsgp_ctx {
-  gsgp_config cfg{};
-  std::string err;
-  int state = 0;   // 0 created, 1 loaded, 2 initialised
-  int device = -1;
-  cudaStream_t stream = nullptr;
-  cudaStream_t cap_stream = nullptr;
-
-  // fitness cases
-  int l = 0;
-  int64_t n_tr = 0, n_te = 0, N = 0, n_pad = 0;
-  float *X = nullptr;   // [l][n_pad]
-  float *t = nullptr;   // [n_pad]
-
-  // run state
-  int Kp = 0, Kr = 0;
-  int tiles_interp = 0;   // 1024-case chunks of a semantic row
-  // generation loop: path 1 = persistent cooperative kernel, 2 = chained
-  // select/stream/final launches; shape = (float4 chunks per thread,
-  // offspring per CTA); grid = CTAs of the persistent kernel
-  int path = 1;
-  GenShape shape{1, 2};
-  int grid = 0;
-  int forced_path = 0;       // gsgp_set_evolve_shape: 0 = choose
-  GenShape forced{0, 0};     // {0, 0} = autotune within the path
-  bool shape_ready = false;
-  GridSync *gs = nullptr;
-  ulonglong2 *cta_min = nullptr, *cta_max = nullptr;
-  int cta_cap = 0;
-  int *bk_perm = nullptr;    // state snapshot used while autotuning
-  double *bk_fit = nullptr, *bk_fit_te = nullptr;
-  DevState *bk_state = nullptr;
-  int64_t layout_key[7] = {0, 0, 0, 0, 0, 0, 0};
-  int *P_genes = nullptr, *P_len = nullptr, *R_genes = nullptr, *R_len = nullptr;
-  float *P_consts = nullptr, *R_consts = nullptr;
-  float *pool = nullptr;
-  void *sigR = nullptr;
-  int *perm = nullptr;
-  double *fit = nullptr, *fit_te = nullptr;
-  double2 *partial = nullptr;
-  int4 *sel = nullptr;
-  float *sel_ms = nullptr;
-  DevState *dstate = nullptr;
-  int4 *trace = nullptr;
-  double2 *best_log = nullptr;
-  int gcap = 0;
-  int4 *lineage = nullptr;
-  int lineage_cap = 0;
-  int *d_anc = nullptr;
-  unsigned *d_flag = nullptr;
-  int gen = 0;
-
-  // CUDA graph of `graph_u` generations, replayed by gsgp_evolve; when built
-  // for timing it records an event before and after every stream launch
-  cudaGraph_t graph = nullptr;
-  cudaGraphExec_t gexec = nullptr;
-  int graph_u = 0;
-  bool graph_timed = false;
-  bool graph_dirty = true;
-  std::vector<cudaGraphNode_t> ev_nodes;   // [2 * graph_u] start/stop record nodes
-  std::vector<cudaEvent_t> ev_marks;       // events the nodes were captured with
-
-  // stream-kernel timing
-  bool timing = false;
-  std::vector<cudaEvent_t> ev0, ev1;
-  int ev_used = 0;
-
-  // rebuilt best model (valid while model_gen == gen)
-  int model_gen = -1;
-  int best_slot = 0, ancestor = 0;
-  double best_tr = 0.0, best_te = 0.0;
-  std::vector<int4> h_lineage;
-  std::vector<double> coef;
-  int *d_terms = nullptr;
-  double *d_coef = nullptr;
-  int terms_cap = 0;
-  int n_terms = 0;
-
-  int64_t launches = 0;
-  int64_t dev_bytes = 0;
-  std::unordered_map<void *, size_t> allocs;
-};
-
 // ---------------------------------------------------------------- errors --
-static gsgp_status fail(gsgp_ctx *c, gsgp_status st, const char *fmt, ...) {
+gsgp_status fail(gsgp_ctx *c, gsgp_status st, const char *fmt, ...) {
   if (c) {
     char buf[512];
     va_list ap;
@@ -113,42 +29,11 @@ static gsgp_status fail(gsgp_ctx *c, gsgp_status st, const char *fmt, ...) {
   return st;
 }
 
-static gsgp_status cuda_fail(gsgp_ctx *c, cudaError_t e, const char *what, int line) {
+gsgp_status cuda_fail(gsgp_ctx *c, cudaError_t e, const char *what, int line) {
   cudaGetLastError();
   return fail(c, e == cudaErrorMemoryAllocation ? GSGP_E_OOM : GSGP_E_CUDA, "%s (api.cu:%d): %s",
               what, line, cudaGetErrorString(e));
 }
-
-#define CK(call)                                                      \
-  do {                                                                \
-    cudaError_t e_ = (call);                                          \
-    if (e_ != cudaSuccess) return cuda_fail(c, e_, #call, __LINE__);  \
-  } while (0)
-
-#define LAUNCH(n, call)      \
-  do {                       \
-    CK(call);                \
-    c->launches += (n);      \
-  } while (0)
-
-#define TRY(expr)                                  \
-  do {                                             \
-    gsgp_status s_ = (expr);                       \
-    if (s_ != GSGP_OK) return s_;                  \
-  } while (0)
-
-#define API_GUARD(c)                                                                   \
-  if (!(c)) return GSGP_E_INVALID;                                                     \
-  (c)->err.clear();                                                                    \
-  try {
-#define API_END(c)                                                                     \
-  }                                                                                    \
-  catch (const std::bad_alloc &) {                                                     \
-    return fail((c), GSGP_E_OOM, "host allocation failed");                            \
-  }                                                                                    \
-  catch (...) {                                                                        \
-    return fail((c), GSGP_E_INVALID, "unexpected host exception");                     \
-  }
 
 // ---------------------------------------------------------------- memory --
 static gsgp_status dalloc(gsgp_ctx *c, void **p, size_t bytes) {
@@ -320,7 +205,7 @@ extern "C" const char *gsgp_config_error(const gsgp_config *cfg) {
 
 extern "C" const char *gsgp_last_error(const gsgp_ctx *c) { return c ? c->err.c_str() : ""; }
 
-static gsgp_status use_device(gsgp_ctx *c) {
+gsgp_status use_device(gsgp_ctx *c) {
   if (c->device < 0) CK(cudaGetDevice(&c->device));
   CK(cudaSetDevice(c->device));
   return GSGP_OK;
@@ -425,7 +310,7 @@ extern "C" gsgp_status gsgp_load_device(gsgp_ctx *c, const float *Xtr, const flo
 }
 
 // ------------------------------------------------------------------ init --
-static GenParams gen_params(gsgp_ctx *c) {
+GenParams gen_params(gsgp_ctx *c) {
   GenParams p{};
   p.target = c->t;
   p.pool = c->pool;
@@ -454,7 +339,7 @@ static GenParams gen_params(gsgp_ctx *c) {
   return p;
 }
 
-static gsgp_status ensure_trace(gsgp_ctx *c, int need) {
+gsgp_status ensure_trace(gsgp_ctx *c, int need) {
   if (need <= c->gcap) return GSGP_OK;
   const int m = c->cfg.pop_size;
   int cap = c->gcap ? c->gcap : 64;
@@ -579,13 +464,15 @@ static gsgp_status launch_generation(gsgp_ctx *c, const GenParams &p, cudaStream
 }
 
 // Shapes the autotuner tries: chained path (vec in {1,2,4}, opb in {2,4,8})
-// and persistent path (vec in {1,2}, opb in {1,2,4} for the register stream;
-// vec in {1,2,4}, opb = 0 for the TMA-staged stream); the choice is cached
-// per problem layout for the process.
+// and persistent path (vec in {1,2}, opb in {1,2,4}, the register stream);
+// the choice is cached per problem layout for the process.  The TMA-staged
+// stream (opb = 0) is selectable with gsgp_set_evolve_shape but not a
+// candidate: its one-generation trials can come out ahead while it is slower
+// over whole launches on every measured workload (one CTA per SM, a start-up
+// cost that a one-generation trial hides).
 static const GenShape kChainShapes[] = {{1, 2}, {1, 4}, {1, 8}, {2, 2}, {2, 4},
                                         {2, 8}, {4, 2}, {4, 4}, {4, 8}};
-static const GenShape kPersistShapes[] = {{1, 1}, {1, 2}, {1, 4}, {2, 1}, {2, 2},
-                                          {2, 4}, {1, 0}, {2, 0}, {4, 0}};
+static const GenShape kPersistShapes[] = {{1, 1}, {1, 2}, {1, 4}, {2, 1}, {2, 2}, {2, 4}};
 struct Tuned {
   int path;
   GenShape shape;
@@ -652,7 +539,7 @@ static gsgp_status launch_persist_chunk(gsgp_ctx *c, int G) {
 // generation writes only free rows of the pool, the draws, the partials and
 // this generation's trace and log entries, all of which the real generation
 // rewrites identically.
-static gsgp_status snapshot(gsgp_ctx *c, bool save) {
+gsgp_status ensure_backup(gsgp_ctx *c) {
   const size_t m = (size_t)c->cfg.pop_size;
   if (!c->bk_perm) {
     TRY(dalloc_n(c, &c->bk_perm, 4 * m));
@@ -660,17 +547,23 @@ static gsgp_status snapshot(gsgp_ctx *c, bool save) {
     TRY(dalloc_n(c, &c->bk_fit_te, 2 * m));
     TRY(dalloc_n(c, &c->bk_state, 1));
   }
+  return GSGP_OK;
+}
+
+gsgp_status snapshot(gsgp_ctx *c, bool save, cudaStream_t s) {
+  const size_t m = (size_t)c->cfg.pop_size;
+  TRY(ensure_backup(c));
   const cudaMemcpyKind k = cudaMemcpyDeviceToDevice;
   if (save) {
-    CK(cudaMemcpyAsync(c->bk_perm, c->perm, sizeof(int) * 4 * m, k, c->stream));
-    CK(cudaMemcpyAsync(c->bk_fit, c->fit, sizeof(double) * 2 * m, k, c->stream));
-    CK(cudaMemcpyAsync(c->bk_fit_te, c->fit_te, sizeof(double) * 2 * m, k, c->stream));
-    CK(cudaMemcpyAsync(c->bk_state, c->dstate, sizeof(DevState), k, c->stream));
+    CK(cudaMemcpyAsync(c->bk_perm, c->perm, sizeof(int) * 4 * m, k, s));
+    CK(cudaMemcpyAsync(c->bk_fit, c->fit, sizeof(double) * 2 * m, k, s));
+    CK(cudaMemcpyAsync(c->bk_fit_te, c->fit_te, sizeof(double) * 2 * m, k, s));
+    CK(cudaMemcpyAsync(c->bk_state, c->dstate, sizeof(DevState), k, s));
   } else {
-    CK(cudaMemcpyAsync(c->perm, c->bk_perm, sizeof(int) * 4 * m, k, c->stream));
-    CK(cudaMemcpyAsync(c->fit, c->bk_fit, sizeof(double) * 2 * m, k, c->stream));
-    CK(cudaMemcpyAsync(c->fit_te, c->bk_fit_te, sizeof(double) * 2 * m, k, c->stream));
-    CK(cudaMemcpyAsync(c->dstate, c->bk_state, sizeof(DevState), k, c->stream));
+    CK(cudaMemcpyAsync(c->perm, c->bk_perm, sizeof(int) * 4 * m, k, s));
+    CK(cudaMemcpyAsync(c->fit, c->bk_fit, sizeof(double) * 2 * m, k, s));
+    CK(cudaMemcpyAsync(c->fit_te, c->bk_fit_te, sizeof(double) * 2 * m, k, s));
+    CK(cudaMemcpyAsync(c->dstate, c->bk_state, sizeof(DevState), k, s));
   }
   return GSGP_OK;
 }
@@ -702,12 +595,12 @@ static gsgp_status time_shape(gsgp_ctx *c, int path, const GenShape &sh, float *
   } else {
     c->grid = persist_grid(c, sh);
     st = ensure_cta_arrays(c, c->grid);
-    if (st == GSGP_OK) st = snapshot(c, true);
+    if (st == GSGP_OK) st = snapshot(c, true, c->stream);
     for (int rep = 0; rep < 4 && st == GSGP_OK && e == cudaSuccess; ++rep) {
       e = cudaEventRecord(e0, c->stream);
       if (e == cudaSuccess) st = launch_persist_chunk(c, 1);
       if (st == GSGP_OK && e == cudaSuccess) e = cudaEventRecord(e1, c->stream);
-      if (st == GSGP_OK && e == cudaSuccess) st = snapshot(c, false);
+      if (st == GSGP_OK && e == cudaSuccess) st = snapshot(c, false, c->stream);
       if (st == GSGP_OK && e == cudaSuccess) e = cudaEventSynchronize(e1);
       float ms = 0.f;
       if (st == GSGP_OK && e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);

@@ -51,119 +51,27 @@ __global__ void __launch_bounds__(kSelectThreads) select_kernel(const GenParams 
   griddep_wait();
   griddep_launch();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int m = p.m;
-  if (i >= m) return;
-  const int g = __ldcg(&p.state->gen);
-  const int par = __ldcg(&p.state->parity);
-  const double *F = p.fit + (size_t)par * m;
-  const int *perm = p.perm + (size_t)par * 2 * m;
-  const int orow = __ldcg(perm + m + i);
-  const Draws d = draw_offspring(
-      p, i, g, [&](int slot) { return __ldcg(F + slot); },
-      [&](int slot) { return __ldcg(perm + slot); });
-  p.sel[i] = make_int4(d.prow, orow, d.a, d.b);
-  p.sel_ms[i] = d.ms;
-  p.trace[(size_t)g * m + i] = make_int4(d.parent, d.a, d.b, __float_as_int(d.ms));
+  if (i >= p.m) return;
+  select_offspring(p, i, __ldcg(&p.state->gen), __ldcg(&p.state->parity));
 }
 
 // ------------------------------------------------------------- stream -----
 template <typename SigT, int VEC, int OPB>
 __global__ void __launch_bounds__(kGenThreads) stream_kernel(const GenParams p) {
-  constexpr int W = kGenThreads * 4 * VEC;
-  constexpr int NW = kGenThreads / 32;
-  __shared__ float2 s_sub[OPB][VEC][NW];   // sub-block totals per offspring and chunk
+  __shared__ ItemSums<VEC, OPB> s_sum;
   griddep_wait();
   griddep_launch();
-
-  const int m = p.m;
-  const int groups = (m + OPB - 1) / OPB;
+  const int groups = (p.m + OPB - 1) / OPB;
   const int tile = blockIdx.x / groups;
-  const int grp = blockIdx.x - tile * groups;
-  const int i0 = grp * OPB;
-  const int cnt = min(OPB, m - i0);
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int64_t base = (int64_t)tile * W;
-  const SigT *sig = static_cast<const SigT *>(p.sigma_r);
-
-  int4 sel = __ldcg(p.sel + i0);
-  float ms = __ldcg(p.sel_ms + i0);
-  for (int k = 0; k < cnt; ++k) {
-    const float *src = p.pool + (int64_t)sel.x * p.n_pad;
-    float *dst = p.pool + (int64_t)sel.y * p.n_pad;
-    const SigT *ra = sig + (int64_t)sel.z * p.n_pad;
-    const SigT *rb = sig + (int64_t)sel.w * p.n_pad;
-    const float step = ms;
-    if (k + 1 < cnt) {   // prefetch the next offspring's draws
-      sel = __ldcg(p.sel + i0 + k + 1);
-      ms = __ldcg(p.sel_ms + i0 + k + 1);
-    }
-#pragma unroll
-    for (int v = 0; v < VEC; ++v) {
-      // chunk v = cases [base + 1024 v, base + 1024 (v + 1)): sub-block = warp,
-      // 4 consecutive cases per lane, as in every other kernel
-      const int64_t j0 = base + v * 1024 + tid * 4;
-      float str = 0.f, ste = 0.f;
-      if (j0 < p.n_pad) mutate4<SigT>(p, src, dst, ra, rb, j0, step, str, ste);
-      const float2 sub = subblock_sum(str, ste);
-      if (lane == 0) s_sub[k][v][warp] = sub;
-    }
-  }
+  const int i0 = (blockIdx.x - tile * groups) * OPB;
+  const int cnt = min(OPB, p.m - i0);
+  stream_item<SigT, VEC, OPB>(p, tile, i0, cnt, __ldcg(p.sel + i0), __ldcg(p.sel_ms + i0), s_sum);
   __syncthreads();
-  for (int e = tid; e < cnt * VEC; e += kGenThreads) {
-    const int k = e / VEC, v = e - k * VEC;
-    if (tile * VEC + v < p.tiles)
-      p.partial[(size_t)(i0 + k) * p.tiles + tile * VEC + v] = chunk_total(s_sub[k][v]);
-  }
+  item_partials<VEC, OPB>(p, tile, i0, cnt, s_sum);
 }
 
 // -------------------------------------------------------------- final -----
 constexpr int kFinalWarps = kFinalThreads / 32;
-
-// Survival with elitism for the whole population, run by the last CTA.
-__device__ void survive(const GenParams &p, int g, int par) {
-  __shared__ unsigned long long s_v[kFinalThreads];
-  __shared__ int s_i[kFinalThreads];
-  const int m = p.m;
-  const double *FT = p.fit + (size_t)par * m;
-  const double *FO = p.fit + (size_t)(par ^ 1) * m;
-  double fbp, fbo, fw;
-  int bP, bO, w;
-  block_arg<false>(FT, m, s_v, s_i, fbp, bP);
-  block_arg<false>(FO, m, s_v, s_i, fbo, bO);
-  block_arg<true>(FO, m, s_v, s_i, fw, w);
-  const bool elite = p.elitism && fbp < fbo;
-  const int *cur = p.perm + (size_t)par * 2 * m;
-  int *nxt = p.perm + (size_t)(par ^ 1) * 2 * m;
-  for (int i = threadIdx.x; i < m; i += blockDim.x) {
-    const int ph = __ldcg(cur + i), fr = __ldcg(cur + m + i);
-    nxt[i] = fr;       // offspring i becomes population slot i
-    nxt[m + i] = ph;   // the parents' rows are free for the next offspring
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double *fit_o = p.fit + (size_t)(par ^ 1) * m;
-    double *fte_o = p.fit_te + (size_t)(par ^ 1) * m;
-    int best = bO;
-    double btr = fbo;
-    double bte = __ldcg(fte_o + bO);
-    if (elite) {
-      nxt[w] = __ldcg(cur + bP);
-      nxt[m + bP] = __ldcg(cur + m + w);
-      const double te = __ldcg(p.fit_te + (size_t)par * m + bP);
-      fit_o[w] = fbp;
-      fte_o[w] = te;
-      p.trace[(size_t)g * m + w] = make_int4(bP, -1, -1, 0);
-      best = w;
-      btr = fbp;
-      bte = te;
-    }
-    p.best_log[g] = make_double2(btr, bte);
-    p.state->best_slot = best;
-    p.state->done = 0u;
-    p.state->parity = par ^ 1;
-    p.state->gen = g + 1;
-  }
-}
 
 __global__ void __launch_bounds__(kFinalThreads) final_kernel(const GenParams p) {
   __shared__ int s_last;
@@ -190,7 +98,7 @@ __global__ void __launch_bounds__(kFinalThreads) final_kernel(const GenParams p)
     __threadfence();
   }
   __syncthreads();
-  if (s_last) survive(p, g, par);
+  if (s_last) survive_population(p, g, par);
 }
 
 // ------------------------------------------------------------ launches -----

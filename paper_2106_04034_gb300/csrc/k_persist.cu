@@ -34,59 +34,12 @@
 // CTAs are co-resident.  The selection runs on the first CTAs and the
 // persisting of the slot-to-row map on the last ones, so that CTAs arrive at
 // the barriers spread out in time rather than all at once.
+#include "gridsync.cuh"
 #include "kernels.cuh"
 #include "reduce.cuh"
 #include "stream.cuh"
 
 namespace gsgp {
-
-constexpr unsigned kSpinLimit = 1u << 24;   // ~1 s of 32-64 ns naps
-
-__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p) {
-  unsigned v;
-  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-
-__device__ __forceinline__ int ld_relaxed_s32(const int *p) {
-  int v;
-  asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-
-// Bounded wait until *p >= target; false (and the sticky error word set)
-// when the bound is hit or another CTA already gave up.
-__device__ __forceinline__ bool wait_at_least(const unsigned *p, unsigned target, GridSync *gs) {
-  unsigned spins = 0;
-  while (ld_acquire_u32(p) < target) {
-    if (ld_relaxed_s32(&gs->err) != 0) return false;
-    if (++spins > kSpinLimit) {
-      atomicExch(&gs->err, 1);
-      return false;
-    }
-    __nanosleep(64);
-  }
-  return true;
-}
-
-// Grid-wide barrier: every CTA adds one arrival to the counter and waits for
-// epoch * grid arrivals (the counter is zeroed before each launch).  A
-// two-level variant (groups of CTAs, one global arrival per group) measured
-// slower here: each extra dependent round trip costs more than the
-// contention it removes.  Returns false when the grid must stop.
-__device__ __forceinline__ bool grid_sync(GridSync *gs, unsigned &epoch, int *s_ok) {
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    ++epoch;
-    __threadfence();
-    atomicAdd(&gs->count, 1u);
-    const bool ok = wait_at_least(&gs->count, epoch * gridDim.x, gs);
-    __threadfence();
-    *s_ok = ok;
-  }
-  __syncthreads();
-  return *s_ok != 0;
-}
 
 // Warp-wide arg-min and arg-max of (key, index) pairs (first index on ties);
 // every lane returns the warp's result.
@@ -308,7 +261,7 @@ template <typename SigT, int VEC, int OPB>
 __global__ void __launch_bounds__(kGenThreads, 4) persist_kernel(const GenParams p, PersistArgs x) {
   constexpr int NW = kGenThreads / 32;
   constexpr int W = 1024 * VEC;
-  __shared__ float2 s_sub[2][OPB][VEC][NW];   // sub-block totals, double-buffered per item
+  __shared__ ItemSums<VEC, OPB> s_sum[2];   // sub-block totals, double-buffered per item
   __shared__ ulonglong2 s_min[32], s_max[32];
   __shared__ double2 s_sse[NW];
   __shared__ int s_ok;
@@ -318,11 +271,9 @@ __global__ void __launch_bounds__(kGenThreads, 4) persist_kernel(const GenParams
   if (ld_relaxed_s32(&gs->err) != 0) return;   // an earlier launch failed
   const int m = p.m;
   const int nb = gridDim.x, b = blockIdx.x, tid = threadIdx.x;
-  const int lane = tid & 31, warp = tid >> 5;
   const int groups = (m + OPB - 1) / OPB;
   const int tiles = (int)((p.n_pad + W - 1) / W);
   const int items = tiles * groups;
-  const SigT *sig = static_cast<const SigT *>(p.sigma_r);
   unsigned epoch = 0;
 
   if (tid == 0) {
@@ -359,41 +310,18 @@ __global__ void __launch_bounds__(kGenThreads, 4) persist_kernel(const GenParams
         const int tile = item / groups;
         const int i0 = (item - tile * groups) * OPB;
         const int cnt = min(OPB, m - i0);
-        const int64_t base_case = (int64_t)tile * W;
-        int4 sel = sel_next;
-        float ms = ms_next;
+        const int4 sel = sel_next;
+        const float ms = ms_next;
         if (item + nb < items) {
           const int i0n = ((item + nb) % groups) * OPB;
           sel_next = __ldcg(p.sel + i0n);
           ms_next = __ldcg(p.sel_ms + i0n);
         }
-        for (int k = 0; k < cnt; ++k) {
-          const float *src = p.pool + (int64_t)sel.x * p.n_pad;
-          float *dst = p.pool + (int64_t)sel.y * p.n_pad;
-          const SigT *ra = sig + (int64_t)sel.z * p.n_pad;
-          const SigT *rb = sig + (int64_t)sel.w * p.n_pad;
-          const float step = ms;
-          if (k + 1 < cnt) {
-            sel = __ldcg(p.sel + i0 + k + 1);
-            ms = __ldcg(p.sel_ms + i0 + k + 1);
-          }
-#pragma unroll
-          for (int v = 0; v < VEC; ++v) {
-            const int64_t j0 = base_case + v * 1024 + tid * 4;
-            float str = 0.f, ste = 0.f;
-            if (j0 < p.n_pad) mutate4<SigT>(p, src, dst, ra, rb, j0, step, str, ste);
-            const float2 sub = subblock_sum(str, ste);
-            if (lane == 0) s_sub[buf][k][v][warp] = sub;
-          }
-        }
+        stream_item<SigT, VEC, OPB>(p, tile, i0, cnt, sel, ms, s_sum[buf]);
         // one barrier per item; the other buffer is written by the next item,
         // and this one again only after the next item's barrier
         __syncthreads();
-        for (int e = tid; e < cnt * VEC; e += kGenThreads) {
-          const int k = e / VEC, v = e - k * VEC;
-          if (tile * VEC + v < p.tiles)
-            p.partial[(size_t)(i0 + k) * p.tiles + tile * VEC + v] = chunk_total(s_sub[buf][k][v]);
-        }
+        item_partials<VEC, OPB>(p, tile, i0, cnt, s_sum[buf]);
       }
     }
     if (!grid_sync(gs, epoch, &s_ok)) return;

@@ -66,6 +66,28 @@ int persist_max_grid(int sigma_bf16, const GenShape &sh);
 cudaError_t launch_persist(const GenParams &p, const PersistArgs &x, int sigma_bf16,
                            const GenShape &sh, int grid, cudaStream_t s);
 
+// Batched persistent kernel (k_batch.cu): up to kBatchRunsPerLaunch
+// independent runs advance G generations in one cooperative launch.  The
+// runs' generation parameters and the offsets of their offspring and stream
+// items (tiles of 1024 * vec cases x groups of opb offspring) in the
+// flattened work lists travel in the kernel's parameter block, so that the
+// kernel reads them, as the single-run kernel reads its GenParams, through
+// the constant cache (uniform per CTA) instead of holding them in registers.
+constexpr int kBatchRunsPerLaunch = 160;   // keeps the parameter block under 32 KB
+struct BatchArgs {
+  GenParams runs[kBatchRunsPerLaunch];
+  int m_off[kBatchRunsPerLaunch + 1];      // ascending, m_off[0] = 0
+  int item_off[kBatchRunsPerLaunch + 1];   // ascending, item_off[0] = 0
+  GridSync *gs;
+  int R;
+  int G;
+};
+static_assert(sizeof(BatchArgs) < 32000, "kernel parameter block limit");
+bool batch_shape_supported(const GenShape &sh);
+int batch_max_grid(int sigma_bf16, const GenShape &sh);
+cudaError_t launch_batch(const BatchArgs &a, int sigma_bf16, const GenShape &sh, int grid,
+                         cudaStream_t s);
+
 cudaError_t launch_lineage(const int4 *trace, int m, int G, const DevState *state, int4 *lineage,
                            int *ancestor, cudaStream_t s);
 

@@ -150,4 +150,126 @@ __device__ __forceinline__ double2 chunk_total(const float2 *sub) {
   return make_double2((double)a, (double)b);
 }
 
+// Selection of offspring slot i at generation g from the population of
+// parity par whose tables are complete in memory (Algorithm 1, "Selection"
+// and the draws of "GSM"): writes the draws used by the stream (parent row,
+// offspring row, rt1, rt2, step) and the trace entry (parent slot, rt1, rt2,
+// step bits).
+__device__ __forceinline__ void select_offspring(const GenParams &p, int i, int g, int par) {
+  const int m = p.m;
+  const double *F = p.fit + (size_t)par * m;
+  const int *perm = p.perm + (size_t)par * 2 * m;
+  const int orow = __ldcg(perm + m + i);
+  const Draws d = draw_offspring(
+      p, i, g, [&](int slot) { return __ldcg(F + slot); },
+      [&](int slot) { return __ldcg(perm + slot); });
+  p.sel[i] = make_int4(d.prow, orow, d.a, d.b);
+  p.sel_ms[i] = d.ms;
+  p.trace[(size_t)g * m + i] = make_int4(d.parent, d.a, d.b, __float_as_int(d.ms));
+}
+
+// Sub-block totals of one stream item: [offspring][chunk][sub-block].
+template <int VEC, int OPB>
+using ItemSums = float2[OPB][VEC][kGenThreads / 32];
+
+// Mutation stream of one item: offspring i0 .. i0 + cnt - 1 (cnt <= OPB) of
+// run p over the cases [tile * 1024 VEC, (tile + 1) * 1024 VEC), all 256
+// threads of the CTA taking part.  sel / ms are the draws of offspring i0;
+// those of the next offspring are loaded while the current one streams.
+// Warp w leaves the total of sub-block w of chunk v of offspring k in
+// sum[k][v][w]; after a barrier item_partials finishes the chunk sums.
+template <typename SigT, int VEC, int OPB>
+__device__ __forceinline__ void stream_item(const GenParams &p, int tile, int i0, int cnt,
+                                            int4 sel, float ms, ItemSums<VEC, OPB> &sum) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const SigT *sig = static_cast<const SigT *>(p.sigma_r);
+  const int64_t base = (int64_t)tile * (1024 * VEC);
+  for (int k = 0; k < cnt; ++k) {
+    const float *src = p.pool + (int64_t)sel.x * p.n_pad;
+    float *dst = p.pool + (int64_t)sel.y * p.n_pad;
+    const SigT *ra = sig + (int64_t)sel.z * p.n_pad;
+    const SigT *rb = sig + (int64_t)sel.w * p.n_pad;
+    const float step = ms;
+    if (k + 1 < cnt) {
+      sel = __ldcg(p.sel + i0 + k + 1);
+      ms = __ldcg(p.sel_ms + i0 + k + 1);
+    }
+#pragma unroll
+    for (int v = 0; v < VEC; ++v) {
+      // chunk v: sub-block = warp, 4 consecutive cases per lane
+      const int64_t j0 = base + v * 1024 + tid * 4;
+      float str = 0.f, ste = 0.f;
+      if (j0 < p.n_pad) mutate4<SigT>(p, src, dst, ra, rb, j0, step, str, ste);
+      const float2 t = subblock_sum(str, ste);
+      if (lane == 0) sum[k][v][warp] = t;
+    }
+  }
+}
+
+// Chunk partials of one stream item from its sub-block totals (after a
+// barrier that follows stream_item).
+template <int VEC, int OPB>
+__device__ __forceinline__ void item_partials(const GenParams &p, int tile, int i0, int cnt,
+                                              const ItemSums<VEC, OPB> &sum) {
+  for (int e = threadIdx.x; e < cnt * VEC; e += kGenThreads) {
+    const int k = e / VEC, v = e - k * VEC;
+    const int chunk = tile * VEC + v;
+    if (chunk < p.tiles)
+      p.partial[(size_t)(i0 + k) * p.tiles + chunk] = chunk_total(sum[k][v]);
+  }
+}
+
+// Survival with elitism (Algorithm 1, "Survival") of run p by the whole CTA
+// (blockDim.x = 256), from the fitness tables in memory: b_P = argmin parent
+// fitness, b_O = argmin offspring fitness, w = argmax offspring fitness
+// (first index on ties).  If F_T[b_P] < F_O[b_O] slot w takes parent b_P's
+// row, fitness and an elite trace entry.  No row is copied: population
+// slots map to rows of a pool of 2m rows, and survival rewrites that map
+// (the paper's pointer swap of S_T and S_O).  Writes the best-of-generation
+// log and advances the run's generation counter and parity.
+static __device__ void survive_population(const GenParams &p, int g, int par) {
+  __shared__ unsigned long long s_v[kGenThreads];
+  __shared__ int s_i[kGenThreads];
+  const int m = p.m;
+  const double *FT = p.fit + (size_t)par * m;
+  const double *FO = p.fit + (size_t)(par ^ 1) * m;
+  double fbp, fbo, fw;
+  int bP, bO, w;
+  block_arg<false>(FT, m, s_v, s_i, fbp, bP);
+  block_arg<false>(FO, m, s_v, s_i, fbo, bO);
+  block_arg<true>(FO, m, s_v, s_i, fw, w);
+  const bool elite = p.elitism && fbp < fbo;
+  const int *cur = p.perm + (size_t)par * 2 * m;
+  int *nxt = p.perm + (size_t)(par ^ 1) * 2 * m;
+  for (int i = threadIdx.x; i < m; i += blockDim.x) {
+    const int ph = __ldcg(cur + i), fr = __ldcg(cur + m + i);
+    nxt[i] = fr;       // offspring i becomes population slot i
+    nxt[m + i] = ph;   // the parents' rows are free for the next offspring
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double *fit_o = p.fit + (size_t)(par ^ 1) * m;
+    double *fte_o = p.fit_te + (size_t)(par ^ 1) * m;
+    int best = bO;
+    double btr = fbo;
+    double bte = __ldcg(fte_o + bO);
+    if (elite) {
+      nxt[w] = __ldcg(cur + bP);
+      nxt[m + bP] = __ldcg(cur + m + w);
+      const double te = __ldcg(p.fit_te + (size_t)par * m + bP);
+      fit_o[w] = fbp;
+      fte_o[w] = te;
+      p.trace[(size_t)g * m + w] = make_int4(bP, -1, -1, 0);
+      best = w;
+      btr = fbp;
+      bte = te;
+    }
+    p.best_log[g] = make_double2(btr, bte);
+    p.state->best_slot = best;
+    p.state->done = 0u;
+    p.state->parity = par ^ 1;
+    p.state->gen = g + 1;
+  }
+}
+
 }  // namespace gsgp

@@ -47,9 +47,10 @@ def test_struct_layouts_match_the_header(lib, tmp_path):
 #include <stddef.h>
 #include "gsgp.h"
 int main(void) {
-  printf("%zu %zu %zu %zu %zu %zu %zu\\n", sizeof(gsgp_config), sizeof(gsgp_trace),
+  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(gsgp_config), sizeof(gsgp_trace),
          sizeof(gsgp_info), offsetof(gsgp_config, stream), offsetof(gsgp_trace, coef),
-         offsetof(gsgp_trace, sigma_dtype), offsetof(gsgp_info, device_bytes));
+         offsetof(gsgp_trace, sigma_dtype), offsetof(gsgp_info, device_bytes),
+         sizeof(gsgp_batch_info), offsetof(gsgp_batch_info, updates_per_generation));
   return 0;
 }
 """)
@@ -58,7 +59,8 @@ int main(void) {
     got = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True,
                                           check=True).stdout.split()]
     want = [C.sizeof(B.Config), C.sizeof(B.Trace), C.sizeof(B.Info), B.Config.stream.offset,
-            B.Trace.coef.offset, B.Trace.sigma_dtype.offset, B.Info.device_bytes.offset]
+            B.Trace.coef.offset, B.Trace.sigma_dtype.offset, B.Info.device_bytes.offset,
+            C.sizeof(B.BatchInfo), B.BatchInfo.updates_per_generation.offset]
     assert got == want
 
 
@@ -134,3 +136,32 @@ def test_missing_library_fails_loudly(tmp_path, monkeypatch):
     monkeypatch.setattr(B, "_lib", None)
     with pytest.raises(ImportError):
         B.load_library(str(tmp_path / "libgsgp.so"))
+
+
+def test_batch_arguments_and_state_without_device(lib):
+    """gsgp_batch_create checks its arguments and the runs' state on the host
+    before any device call."""
+    out = C.c_void_p()
+    runs = [pkg.Run(pop_size=8, n_random_trees=4) for _ in range(2)]
+    arr = (C.c_void_p * 2)(runs[0].ctx.value, runs[1].ctx.value)
+    assert lib.gsgp_batch_create(arr, 2, None) == B.E_INVALID
+    assert lib.gsgp_batch_create(None, 2, C.byref(out)) == B.E_INVALID
+    assert lib.gsgp_batch_create(arr, 0, C.byref(out)) == B.E_INVALID
+    assert lib.gsgp_batch_create(arr, 1025, C.byref(out)) == B.E_INVALID
+    dup = (C.c_void_p * 2)(runs[0].ctx.value, runs[0].ctx.value)
+    assert lib.gsgp_batch_create(dup, 2, C.byref(out)) == B.E_INVALID
+    with_null = (C.c_void_p * 2)(runs[0].ctx.value, None)
+    assert lib.gsgp_batch_create(with_null, 2, C.byref(out)) == B.E_INVALID
+    # runs that are not initialised
+    assert lib.gsgp_batch_create(arr, 2, C.byref(out)) == B.E_STATE
+    assert not out.value
+    with pytest.raises(pkg.GsgpError) as e:
+        pkg.Batch(runs)
+    assert e.value.status == B.E_STATE
+    assert lib.gsgp_batch_evolve(None, 1, None, None) == B.E_INVALID
+    assert lib.gsgp_batch_set_shape(None, 1, 1) == B.E_INVALID
+    assert lib.gsgp_batch_get_info(None, None) == B.E_INVALID
+    assert lib.gsgp_batch_last_error(None) == b""
+    lib.gsgp_batch_destroy(None)
+    for r in runs:
+        r.close()

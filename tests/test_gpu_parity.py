@@ -377,4 +377,5 @@ def test_default_path_is_persistent():
     run.evolve(3)
     info = run.info()
     assert info.evolve_path == pkg.PATH_PERSISTENT and info.evolve_grid >= 1
+    assert info.evolve_offspring_per_cta > 0     # the autotuner picks a register-stream shape
     run.close()
