@@ -107,6 +107,10 @@ static void free_run_buffers(gsgp_ctx *c) {
   dfree(c, c->trace);
   dfree(c, c->best_log);
   dfree(c, c->lineage);
+  dfree(c, c->lin_jump);
+  dfree(c, c->lin_start);
+  c->lin_jump_cap = 0;
+  c->lin_start_cap = 0;
   dfree(c, c->d_anc);
   dfree(c, c->d_terms);
   dfree(c, c->d_coef);
@@ -852,7 +856,20 @@ static gsgp_status build_model(gsgp_ctx *c) {
     TRY(dalloc_n(c, &c->lineage, 64));
     c->lineage_cap = 64;
   }
-  LAUNCH(1, launch_lineage(c->trace, m, G, c->dstate, c->lineage, c->d_anc, c->stream));
+  const int L = lineage_segment(G > 0 ? G : 1);
+  const int nseg = G > 0 ? (G + L - 1) / L : 1;
+  if ((int64_t)nseg * m > c->lin_jump_cap) {
+    dfree(c, c->lin_jump);
+    TRY(dalloc_n(c, &c->lin_jump, (size_t)nseg * m));
+    c->lin_jump_cap = (int64_t)nseg * m;
+  }
+  if (nseg > c->lin_start_cap) {
+    dfree(c, c->lin_start);
+    TRY(dalloc_n(c, &c->lin_start, (size_t)nseg));
+    c->lin_start_cap = nseg;
+  }
+  LAUNCH(3, launch_lineage(c->trace, m, G, c->dstate, c->lineage, c->d_anc, c->lin_jump,
+                           c->lin_start, c->stream));
   c->h_lineage.resize((size_t)G);
   DevState st{};
   if (G > 0)

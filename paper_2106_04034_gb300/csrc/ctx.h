@@ -60,6 +60,10 @@ struct gsgp_ctx {
   int gcap = 0;
   int4 *lineage = nullptr;
   int lineage_cap = 0;
+  int *lin_jump = nullptr;    // scratch of the segmented lineage walk
+  int *lin_start = nullptr;
+  int64_t lin_jump_cap = 0;
+  int lin_start_cap = 0;
   int *d_anc = nullptr;
   unsigned *d_flag = nullptr;
   int gen = 0;

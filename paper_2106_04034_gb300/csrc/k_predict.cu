@@ -6,24 +6,76 @@
 namespace gsgp {
 
 // Walk the trace back from the best slot: entry (g, slot) names the slot of
-// generation g-1 it came from.  One thread; the trace of a run is small and
-// L2-resident.
-__global__ void lineage_kernel(const int4 *__restrict__ trace, int m, int G,
-                               const DevState *__restrict__ state, int4 *__restrict__ lineage,
-                               int *__restrict__ ancestor) {
+// generation g-1 it came from, so lineage[g] = trace[g][slot_g] with
+// slot_{G-1} = best and slot_{g-1} = lineage[g].parent; the slot left after
+// generation 0 is the ancestor in P.  The walk is a chain of G dependent
+// loads; it is split into segments of L generations:
+//   1. jump: for every segment s and every slot, the slot L generations
+//      back (nseg * m independent walks of L steps);
+//   2. one thread follows the jumps from the best slot (nseg steps) and
+//      records the slot each segment starts from;
+//   3. one thread per segment walks it (L steps) writing its lineage entries.
+// Three chains of about sqrt(G) loads instead of one of G.
+__global__ void lineage_jump_kernel(const int4 *__restrict__ trace, int m, int G, int L, int nseg,
+                                    int *__restrict__ jump) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (int64_t)nseg * m) return;
+  const int seg = (int)(t / m);
+  int slot = (int)(t - (int64_t)seg * m);
+  const int g0 = G - 1 - seg * L;
+  const int g1 = g0 - L + 1 > 0 ? g0 - L + 1 : 0;
+  for (int g = g0; g >= g1; --g) slot = __ldg(&trace[(size_t)g * m + slot]).x;
+  jump[t] = slot;
+}
+
+__global__ void lineage_follow_kernel(const int *__restrict__ jump, int m, int nseg,
+                                      const DevState *__restrict__ state, int *__restrict__ start,
+                                      int *__restrict__ ancestor) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   int slot = state->best_slot;
-  for (int g = G - 1; g >= 0; --g) {
-    const int4 e = trace[(size_t)g * m + slot];
-    lineage[g] = e;
-    slot = e.x;
+  for (int s = 0; s < nseg; ++s) {
+    start[s] = slot;
+    slot = jump[(size_t)s * m + slot];
   }
   *ancestor = slot;
 }
 
+__global__ void lineage_walk_kernel(const int4 *__restrict__ trace, int m, int G, int L, int nseg,
+                                    const int *__restrict__ start, int4 *__restrict__ lineage) {
+  const int seg = blockIdx.x * blockDim.x + threadIdx.x;
+  if (seg >= nseg) return;
+  int slot = start[seg];
+  const int g0 = G - 1 - seg * L;
+  const int g1 = g0 - L + 1 > 0 ? g0 - L + 1 : 0;
+  for (int g = g0; g >= g1; --g) {
+    const int4 e = __ldg(&trace[(size_t)g * m + slot]);
+    lineage[g] = e;
+    slot = e.x;
+  }
+}
+
+int lineage_segment(int G) {
+  int L = 8;
+  while (L * L < G && L < 256) L *= 2;
+  return L;
+}
+
 cudaError_t launch_lineage(const int4 *trace, int m, int G, const DevState *state, int4 *lineage,
-                           int *ancestor, cudaStream_t s) {
-  lineage_kernel<<<1, 32, 0, s>>>(trace, m, G, state, lineage, ancestor);
+                           int *ancestor, int *jump, int *start, cudaStream_t s) {
+  if (G <= 0) {   // no generation: the ancestor is the best slot itself
+    lineage_follow_kernel<<<1, 32, 0, s>>>(jump, m, 0, state, start, ancestor);
+    return cudaGetLastError();
+  }
+  const int L = lineage_segment(G);
+  const int nseg = (G + L - 1) / L;
+  const int64_t jobs = (int64_t)nseg * m;
+  lineage_jump_kernel<<<(unsigned)((jobs + 255) / 256), 256, 0, s>>>(trace, m, G, L, nseg, jump);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  lineage_follow_kernel<<<1, 32, 0, s>>>(jump, m, nseg, state, start, ancestor);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  lineage_walk_kernel<<<(nseg + 127) / 128, 128, 0, s>>>(trace, m, G, L, nseg, start, lineage);
   return cudaGetLastError();
 }
 
@@ -96,32 +148,53 @@ __device__ float eval_program32(const int *__restrict__ genes, const float *__re
 // float64.  With bf16 storage q(sigma(R_k(x))) is the value training used:
 // R_k evaluated in float32, the logistic in float32, rounded to bf16
 // (nearest-even), so the rebuilt model reproduces the training semantics.
-__global__ void __launch_bounds__(128) predict_kernel(const PredictParams p) {
-  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= p.n) return;
+//
+// A CTA takes 32 cases (one per lane) and its kPredWarps warps split the
+// terms: warp w adds terms w, w + kPredWarps, ... in order, so every warp
+// evaluates one program at a time for its 32 cases (uniform gene stream).
+// The last warp also evaluates the ancestor.  The case's value is then the
+// ancestor plus the warps' sums, added in warp order (a fixed order).
+constexpr int kPredWarps = 16;
+
+__global__ void __launch_bounds__(kPredWarps * 32) predict_kernel(const PredictParams p) {
+  __shared__ double s_acc[kPredWarps][32];
+  __shared__ double s_anc[32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t j = (int64_t)blockIdx.x * 32 + lane;
+  const bool valid = j < p.n;
+  const int64_t jj = valid ? j : 0;   // padding lanes evaluate case 0 and store nothing
   const double eps = (double)p.protect_eps;
-  double y = eval_program64(p.anc_genes, p.anc_consts, p.anc_len, p.X, p.n_pad, j, eps);
-  for (int q = 0; q < p.nk; ++q) {
+  double acc = 0.0;
+  for (int q = warp; q < p.nk; q += kPredWarps) {
     const int k = p.terms[q];
     double sg;
     if (p.sigma_bf16) {
       const float v = eval_program32(p.rt_genes + (size_t)k * p.Kr, p.rt_consts + (size_t)k * p.Kr,
-                                     p.rt_len[k], p.X, p.n_pad, j, p.protect_eps);
+                                     p.rt_len[k], p.X, p.n_pad, jj, p.protect_eps);
       sg = (double)__bfloat162float(__float2bfloat16_rn(1.0f / (1.0f + expf(-v))));
     } else {
       const double v = eval_program64(p.rt_genes + (size_t)k * p.Kr,
-                                      p.rt_consts + (size_t)k * p.Kr, p.rt_len[k], p.X, p.n_pad, j,
+                                      p.rt_consts + (size_t)k * p.Kr, p.rt_len[k], p.X, p.n_pad, jj,
                                       eps);
       sg = 1.0 / (1.0 + exp(-v));
     }
-    y += p.coef[q] * sg;
+    acc += p.coef[q] * sg;
   }
-  p.y[j] = y;
+  if (warp == kPredWarps - 1)
+    s_anc[lane] = eval_program64(p.anc_genes, p.anc_consts, p.anc_len, p.X, p.n_pad, jj, eps);
+  s_acc[warp][lane] = acc;
+  __syncthreads();
+  if (warp == 0 && valid) {
+    double y = s_anc[lane];
+#pragma unroll
+    for (int w = 0; w < kPredWarps; ++w) y += s_acc[w][lane];
+    p.y[j] = y;
+  }
 }
 
 cudaError_t launch_predict(const PredictParams &p, cudaStream_t s) {
   if (p.n <= 0) return cudaSuccess;
-  predict_kernel<<<(unsigned)((p.n + 127) / 128), 128, 0, s>>>(p);
+  predict_kernel<<<(unsigned)((p.n + 31) / 32), kPredWarps * 32, 0, s>>>(p);
   return cudaGetLastError();
 }
 

@@ -88,8 +88,11 @@ int batch_max_grid(int sigma_bf16, const GenShape &sh);
 cudaError_t launch_batch(const BatchArgs &a, int sigma_bf16, const GenShape &sh, int grid,
                          cudaStream_t s);
 
+// Lineage of the best slot over G generations (k_predict.cu); jump holds
+// ceil(G / lineage_segment(G)) * m ints and start ceil(G / L) ints of scratch.
+int lineage_segment(int G);
 cudaError_t launch_lineage(const int4 *trace, int m, int G, const DevState *state, int4 *lineage,
-                           int *ancestor, cudaStream_t s);
+                           int *ancestor, int *jump, int *start, cudaStream_t s);
 
 struct PredictParams {
   const float *X;      // [l][n_pad] feature-major new cases
