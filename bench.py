@@ -49,6 +49,28 @@ def measured_peak_gbs():
         return 6800.0, "fallback"
 
 
+# ---- replicas: one independent run per rank, no collective on the data path
+def replica_workload(w: W.Workload, rank: int) -> W.Workload:
+    """The workload of rank `rank`: same shapes, its own run index (Philox
+    counter word and data seed), so replicas draw independent data."""
+    return w.replace(run=w.run + rank)
+
+
+def max_over_ranks(x: float, world: int, device="cuda") -> float:
+    """The slowest rank's value (the job's time); identity for one rank."""
+    if world <= 1:
+        return x
+    import torch
+    t = torch.tensor([x], device=device, dtype=torch.float64)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(units_per_rank: float, world: int, seconds: float) -> float:
+    """Whole-job throughput: units all ranks processed / the job's time."""
+    return units_per_rank * world / seconds
+
+
 def profiled_traffic(workload_name: str):
     """DRAM bytes per generation of the generation kernel from the committed
     ncu summary, if it was taken on this workload with the current kernel
@@ -154,7 +176,7 @@ def run_ours(args, rank, world, local_rank):
     w = W.WORKLOADS[args.workload]
     if args.generations:
         w = w.replace(generations=args.generations)
-    w = w.replace(run=rank)
+    w = replica_workload(w, rank)
     G = w.generations
     data = W.make_data(w)
     Xtr, ytr, Xte, yte = data
@@ -206,13 +228,10 @@ def run_ours(args, rank, world, local_rank):
     launches = run.info().kernel_launches - launches0
     ms_total = e0.elapsed_time(e1)
     run.set_kernel_timing(False)
-    if world > 1:
-        t = torch.tensor([ms_total], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms_total = float(t.item())
+    ms_total = max_over_ranks(ms_total, world)
     ms_step = ms_total / args.steps
     updates = float(w.pop_size) * w.n_cases * G
-    value = updates * world / (ms_step / 1e3)
+    value = job_value(updates, world, ms_step / 1e3)
 
     # roofline of the generation kernel: algorithmic bytes / measured duration.
     # The persistent kernel runs up to `per` generations per launch; the
@@ -250,10 +269,7 @@ def run_ours(args, rank, world, local_rank):
         step_host()
     barrier()
     e2e_s = (time.perf_counter() - t0) / args.steps
-    if world > 1:
-        t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks(e2e_s, world)
     h2d = Xtr.nbytes + ytr.nbytes + Xte.nbytes + yte.nbytes + Xte.nbytes
     d2h = w.n_test * 8
     bt = run.best_trace()
@@ -283,7 +299,7 @@ def run_ours(args, rank, world, local_rank):
                                "tile_cases": info.evolve_tile_cases,
                                "offspring_per_cta": info.evolve_offspring_per_cta,
                                "grid": info.evolve_grid}},
-        "e2e": {"value": updates * world / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+        "e2e": {"value": job_value(updates, world, e2e_s), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h)},
         "gpu_launches": int(launches),
         "clocks": clock,
@@ -322,7 +338,7 @@ def run_batched(args, rank, world, local_rank):
     build_library()
     G = args.generations or 500
     nruns = args.batch_runs
-    ws = [w.replace(run=w.run + 1000 * rank)
+    ws = [replica_workload(w, 1000 * rank)
           for w in W.batched_runs(nruns, generations=G, max_train=args.max_train or None)]
     datas = [W.make_data(w) for w in ws]
     devs = [[torch.from_numpy(a).cuda() for a in d] for d in datas]
@@ -370,10 +386,7 @@ def run_batched(args, rank, world, local_rank):
         e1.record(stream)
         barrier()
         ms = e0.elapsed_time(e1)
-        if world > 1:
-            t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            ms = float(t.item())
+        ms = max_over_ranks(ms, world)
         return ms / steps
 
     for _ in range(args.warmup):
@@ -388,7 +401,7 @@ def run_batched(args, rank, world, local_rank):
     batch.set_kernel_timing(False)
     launches = batch.info().kernel_launches + sum(r.info().kernel_launches for r in runs) - launches0
     updates = float(sum(w.pop_size * w.n_cases for w in ws)) * G
-    value = updates * world / (ms_step / 1e3)
+    value = job_value(updates, world, ms_step / 1e3)
 
     # roofline of the batched kernel: algorithmic bytes of every run's
     # generations (distinct parents and random trees read once, offspring
@@ -408,7 +421,7 @@ def run_batched(args, rank, world, local_rank):
     step_sequential()                       # autotunes each run's layout once
     seq_steps = max(1, min(args.steps, 2))
     ms_seq = timed(step_sequential, seq_steps)
-    value_seq = updates * world / (ms_seq / 1e3)
+    value_seq = job_value(updates, world, ms_seq / 1e3)
 
     # end to end through host buffers
     def step_host():
@@ -425,10 +438,7 @@ def run_batched(args, rank, world, local_rank):
         step_host()
     barrier()
     e2e_s = (time.perf_counter() - t0) / args.steps
-    if world > 1:
-        t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks(e2e_s, world)
     h2d = sum(sum(a.nbytes for a in d) + d[2].nbytes for d in datas)
     d2h = sum(w.n_test * 8 for w in ws)
     batch.close()
@@ -464,7 +474,7 @@ def run_batched(args, rank, world, local_rank):
                      "shape": {"tile_cases": info.tile_cases,
                                "offspring_per_cta": info.offspring_per_cta,
                                "grid": info.grid, "graph": bool(info.graph)}},
-        "e2e": {"value": updates * world / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+        "e2e": {"value": job_value(updates, world, e2e_s), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h)},
         "gpu_launches": int(launches),
         "clocks": clock,

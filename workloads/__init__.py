@@ -78,9 +78,11 @@ LARGE = Workload(
     rt_max_depth=6, generations=200, feature_dist="normal", target="monomials",
     noise=0.1, wid=2)
 
+# The precision variant: the same data, programs and draws as LARGE, only
+# sigma(R) stored as bf16, over 2000 generations.
 LARGE_BF16 = LARGE.replace(
     name="large-bf16: LARGE with sigma(R) stored bf16, G=2000",
-    generations=2000, sigma_bf16=True, wid=3)
+    generations=2000, sigma_bf16=True)
 
 WORKLOADS = {"tiny": TINY, "mid": MID, "large": LARGE, "large_bf16": LARGE_BF16}
 
