@@ -40,9 +40,9 @@ from typing import Optional
 
 import numpy as np
 
-from .interp import bf16_round, eval_postfix, pool_semantics, sigma
+from .interp import bf16_round, eval_linear_genome, eval_postfix, pool_semantics, sigma
 from .philox import PURPOSE_POP, PURPOSE_RT, idx, streams_words, u24
-from .trees import rhh_pool
+from .trees import linear_pool, rhh_pool
 
 
 @dataclasses.dataclass
@@ -66,6 +66,8 @@ class Params:
     elitism: bool = True
     sigma_bf16: bool = False
     gsm_sign_plus: bool = False  # the printed "+" form; experiments only
+    init_mode: int = 0           # 0 ramped half-and-half trees, 1 the paper's linear genomes
+    max_genes: int = 127         # genome length k (init_mode 1)
 
 
 def feature_major(X_rows: np.ndarray) -> np.ndarray:
@@ -168,6 +170,12 @@ class GSGP:
     # ---- Algorithm 1, initialisation -------------------------------------
     def create_programs(self):
         p = self.p
+        if p.init_mode == 1:
+            self.P = linear_pool(p.seed, p.run, PURPOSE_POP, p.pop_size, p.max_genes,
+                                 self.n_features, p.const_lo, p.const_hi)
+            self.R = linear_pool(p.seed, p.run, PURPOSE_RT, p.n_random_trees, p.max_genes,
+                                 self.n_features, p.const_lo, p.const_hi)
+            return
         self.P = rhh_pool(p.seed, p.run, PURPOSE_POP, p.pop_size, p.pop_min_depth,
                           p.pop_max_depth, self.n_features, p.p_grow, p.p_feature,
                           p.const_lo, p.const_hi)
@@ -177,9 +185,10 @@ class GSGP:
 
     def compute_semantics(self):
         p = self.p
-        self.S_T = pool_semantics(*self.P, self.X, p.protect_eps)
+        lin = p.init_mode == 1
+        self.S_T = pool_semantics(*self.P, self.X, p.protect_eps, linear=lin)
         self.S_R = pool_semantics(*self.R, self.X, p.protect_eps, logistic=True,
-                                  bf16=p.sigma_bf16)
+                                  bf16=p.sigma_bf16, linear=lin)
 
     def compute_fitness(self):
         self.F_T, self.F_T_te = rmse(self.S_T, self.t, self.n_train)
@@ -291,16 +300,19 @@ def reconstruct(trace, slot: int, n_random_trees: int):
     return slot, c
 
 
-def predict(P, R, ancestor: int, coef, X_fm, protect_eps=1e-3, sigma_bf16=False):
+def predict(P, R, ancestor: int, coef, X_fm, protect_eps=1e-3, sigma_bf16=False,
+            linear=False):
     """Value of the rebuilt model on feature-major cases X_fm (l, n):
-    ancestor(x) + sum_k coef_k * sigma(R_k(x))."""
+    ancestor(x) + sum_k coef_k * sigma(R_k(x)); linear: the programs are
+    linear genomes (skip rule, Out register)."""
+    evaluate = eval_linear_genome if linear else eval_postfix
     gP, cP, lP = P
     L = int(lP[ancestor])
-    y = eval_postfix(gP[ancestor, :L], cP[ancestor, :L], X_fm, protect_eps)
+    y = evaluate(gP[ancestor, :L], cP[ancestor, :L], X_fm, protect_eps)
     gR, cR, lR = R
     for k in np.nonzero(coef)[0]:
         L = int(lR[k])
-        s = sigma(eval_postfix(gR[k, :L], cR[k, :L], X_fm, protect_eps))
+        s = sigma(evaluate(gR[k, :L], cR[k, :L], X_fm, protect_eps))
         if sigma_bf16:
             s = bf16_round(s)
         y = y + coef[k] * s

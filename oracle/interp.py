@@ -118,13 +118,15 @@ def bf16_round(v) -> np.ndarray:
 
 
 def pool_semantics(genes, consts, lengths, X, protect_eps=1e-3, logistic=False,
-                   bf16=False) -> np.ndarray:
+                   bf16=False, linear=False) -> np.ndarray:
     """Semantic matrix of a pool: row i = semantics of program i (Alg. 1,
-    S_T for the population, S_R for the random trees)."""
+    S_T for the population, S_R for the random trees).  linear: the programs
+    are the paper's linear genomes, read with the skip rule and Out."""
     rows = []
+    evaluate = eval_linear_genome if linear else eval_postfix
     for i in range(genes.shape[0]):
         L = int(lengths[i])
-        s = eval_postfix(genes[i, :L], consts[i, :L], X, protect_eps)
+        s = evaluate(genes[i, :L], consts[i, :L], X, protect_eps)
         if logistic:
             s = sigma(s)
             if bf16:
@@ -204,7 +206,7 @@ def postfix_to_tree(genes, consts):
 U32 = 2.0 ** -24          # unit roundoff of float32 round-to-nearest
 
 
-def eval_postfix_fp32_bound(genes, consts, X, protect_eps: float = 1e-3):
+def eval_postfix_fp32_bound(genes, consts, X, protect_eps: float = 1e-3, linear=False):
     """Exact (float64) value of a program and a first-order bound on the
     error of evaluating it in float32 arithmetic, every operation rounded
     once to nearest (running error analysis, Wilkinson).
@@ -217,11 +219,13 @@ def eval_postfix_fp32_bound(genes, consts, X, protect_eps: float = 1e-3):
     infinite where float32 could take the other branch of protected division
     (|b| within its error of eps) or where a magnitude exceeds 1e38 (float32
     overflow), i.e. where the two precisions may legitimately disagree.
-    Returns (value (n,), bound (n,)).
+    linear: a linear genome, read with the skip rule and the Out register
+    (eval_linear_genome).  Returns (value (n,), bound (n,)).
     """
     eps = float(np.float32(protect_eps))
     n = X.shape[1]
     stack = []
+    out = None
     with np.errstate(all="ignore"):
         for g, c in zip(genes, consts):
             g = int(g)
@@ -233,6 +237,8 @@ def eval_postfix_fp32_bound(genes, consts, X, protect_eps: float = 1e-3):
                 continue
             if op == OP_CONST:
                 stack.append((np.full(n, float(c)), np.zeros(n)))
+                continue
+            if linear and len(stack) < 2:
                 continue
             b, eb = stack.pop()
             a, ea = stack.pop()
@@ -254,6 +260,11 @@ def eval_postfix_fp32_bound(genes, consts, X, protect_eps: float = 1e-3):
             e = np.where(np.abs(r) > 1e38, np.inf, e)
             e = np.where(np.isfinite(r), e, np.inf)
             stack.append((r, e))
+            out = (r, e)
+    if linear:
+        if out is not None:
+            return out
+        return stack[-1] if stack else (np.zeros(n), np.zeros(n))
     if len(stack) != 1:
         raise ValueError("program is not well-formed postfix")
     return stack[0]

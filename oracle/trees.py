@@ -98,6 +98,67 @@ def rhh_pool(seed: int, run: int, purpose: int, count: int, dmin: int, dmax: int
     return genes, consts, lengths
 
 
+# ---- the paper's fixed-length linear genome (init_mode 1) -------------------
+#
+# Every gene of a chromosome of K genes is drawn independently: a function
+# with probability 0.8, a feature with probability 0.14, an ephemeral random
+# constant with probability 0.04 (Sec. 2.2, "Initialization").  The printed
+# probabilities add up to 0.98; they are read as relative weights, i.e.
+# divided by 0.98.  Shared contract: gene j of individual i reads words 2j and
+# 2j+1 of the stream (i, 0x80000000 | purpose, run); u24(word 2j) below
+# float32(0.8 / 0.98) makes a function, whose operator is idx(word 2j+1, 4);
+# below float32(0.94 / 0.98) a feature idx(word 2j+1, l); otherwise a
+# constant erc(word 2j+1) in [lo, hi).
+P_FUNCTION = 0.8 / 0.98
+P_FUNCTION_OR_FEATURE = (0.8 + 0.14) / 0.98
+
+
+def linear_genome(seed: int, run: int, purpose: int, i: int, K: int, n_features: int,
+                  const_lo: float, const_hi: float):
+    """Genes (int32 [K]) and constants (float32 [K]) of individual i."""
+    from .philox import stream_words
+    w = stream_words(seed, run, INIT_FLAG | purpose, i, 2 * K)
+    u = u24(w[0::2])                      # gene class words (exact floats)
+    c = w[1::2]                           # operator / feature / constant words
+    is_fun = u < float(np.float32(P_FUNCTION))
+    is_var = ~is_fun & (u < float(np.float32(P_FUNCTION_OR_FEATURE)))
+    is_const = ~is_fun & ~is_var
+    genes = np.where(is_fun, idx(c, 4),
+                     np.where(is_var, OP_VAR | (idx(c, n_features) << 8), OP_CONST))
+    consts = np.zeros(K, dtype=np.float32)
+    for j in np.nonzero(is_const)[0]:
+        consts[j] = erc(int(c[j]), const_lo, const_hi)
+    return genes.astype(np.int32), consts
+
+
+def linear_pool(seed: int, run: int, purpose: int, count: int, K: int, n_features: int,
+                const_lo: float = -1.0, const_hi: float = 1.0):
+    """A pool of linear genomes: (genes [count, K], consts [count, K],
+    lengths [count] = K)."""
+    genes = np.zeros((count, K), dtype=np.int32)
+    consts = np.zeros((count, K), dtype=np.float32)
+    for i in range(count):
+        genes[i], consts[i] = linear_genome(seed, run, purpose, i, K, n_features,
+                                            const_lo, const_hi)
+    return genes, consts, np.full(count, K, dtype=np.int32)
+
+
+def genome_max_stack(genes) -> int:
+    """Deepest stack reached while interpreting a linear genome with the
+    skip rule (a function short of operands leaves the stack as it is)."""
+    sp = best = 0
+    for g in genes:
+        g = int(g)
+        if g == PAD:
+            break
+        if (g & 0xFF) in (OP_CONST, OP_VAR):
+            sp += 1
+            best = max(best, sp)
+        elif sp >= 2:
+            sp -= 1
+    return best
+
+
 def postfix_depth(genes) -> int:
     """Depth of the tree a well-formed postfix program encodes (root = 0)."""
     st = []
