@@ -74,6 +74,18 @@ enum {
 };
 
 enum { GSGP_SIGMA_F32 = 0, GSGP_SIGMA_BF16 = 1 };
+
+/* Program representation of P and R.
+ *   GSGP_INIT_RHH: ramped half-and-half trees emitted in postfix order,
+ *     depths from the config (the default).
+ *   GSGP_INIT_LINEAR: the paper's fixed-length linear genomes (Sec. 2.2,
+ *     "Initialization"): max_genes genes, each independently a function,
+ *     a feature or a constant with weights 0.8 : 0.14 : 0.04.  The
+ *     interpreter skips a function that finds fewer than two operands and
+ *     returns register Out, the last function output ("Interpreter"); a
+ *     genome whose stack would exceed 32 entries is rejected by gsgp_init
+ *     (GSGP_E_INVALID). */
+enum { GSGP_INIT_RHH = 0, GSGP_INIT_LINEAR = 1 };
 enum { GSGP_POOL_POPULATION = 0, GSGP_POOL_RANDOM = 1 };
 
 /* Optional device allocator.  alloc returns device memory of at least
@@ -99,6 +111,8 @@ typedef struct {
   int32_t tournament_size;     /* 0: slot i mutates parent i (no selection) */
   int32_t elitism;             /* 1: keep the best of parents and offspring */
   int32_t sigma_dtype;         /* GSGP_SIGMA_F32 or GSGP_SIGMA_BF16 storage of sigma(R) */
+  int32_t init_mode;           /* GSGP_INIT_RHH or GSGP_INIT_LINEAR (see below) */
+  int32_t max_genes;           /* GSGP_INIT_LINEAR: genome length k, 1 .. 4095 */
   void *stream;                /* cudaStream_t for all device work */
   gsgp_alloc_fn alloc;         /* optional device allocator (see above) */
   gsgp_free_fn free;
@@ -107,8 +121,9 @@ typedef struct {
 
 /* Fill *cfg with defaults: seed 1, run 0, m = 1024, r = 1024, depths 2-6,
  * constants in [-1, 1), p_grow 0.5, p_feature 7/9, protect_eps 1e-3,
- * ms 0.1 fixed, tournament 4, elitism on, float32 sigma, NULL stream and
- * allocator.  No CUDA call. */
+ * ms 0.1 fixed, tournament 4, elitism on, float32 sigma, ramped
+ * half-and-half programs (max_genes 127 for linear genomes), NULL stream
+ * and allocator.  No CUDA call. */
 void gsgp_config_default(gsgp_config *cfg);
 
 /* Reason *cfg would be rejected by gsgp_create, or "" when it is valid.

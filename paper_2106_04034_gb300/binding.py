@@ -21,6 +21,7 @@ STATUS = {0: "GSGP_OK", 1: "GSGP_E_INVALID", 2: "GSGP_E_STATE", 3: "GSGP_E_OOM",
 OK, E_INVALID, E_STATE, E_OOM, E_CUDA, E_TIMEOUT, E_NUMERIC = range(7)
 OP_ADD, OP_SUB, OP_MUL, OP_DIV, OP_CONST, OP_VAR, GENE_PAD = 0, 1, 2, 3, 4, 5, -1
 SIGMA_F32, SIGMA_BF16 = 0, 1
+INIT_RHH, INIT_LINEAR = 0, 1
 POOL_POPULATION, POOL_RANDOM = 0, 1
 PATH_AUTO, PATH_PERSISTENT, PATH_CHAINED = 0, 1, 2
 
@@ -44,6 +45,7 @@ class Config(C.Structure):
         ("p_grow_function", C.c_float), ("p_feature_given_terminal", C.c_float),
         ("protect_eps", C.c_float), ("ms", C.c_float), ("ms_mode", C.c_int32),
         ("tournament_size", C.c_int32), ("elitism", C.c_int32), ("sigma_dtype", C.c_int32),
+        ("init_mode", C.c_int32), ("max_genes", C.c_int32),
         ("stream", C.c_void_p), ("alloc", ALLOC_FN), ("free", FREE_FN),
         ("alloc_user", C.c_void_p),
     ]

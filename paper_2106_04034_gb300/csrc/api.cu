@@ -96,6 +96,7 @@ static void free_run_buffers(gsgp_ctx *c) {
   dfree(c, c->sel);
   dfree(c, c->sel_ms);
   dfree(c, c->dstate);
+  dfree(c, c->d_stack);
   dfree(c, c->gs);
   dfree(c, c->cta_min);
   dfree(c, c->cta_max);
@@ -153,6 +154,8 @@ extern "C" void gsgp_config_default(gsgp_config *cfg) {
   cfg->tournament_size = 4;
   cfg->elitism = 1;
   cfg->sigma_dtype = GSGP_SIGMA_F32;
+  cfg->init_mode = GSGP_INIT_RHH;
+  cfg->max_genes = 127;
 }
 
 static bool prob_ok(float p) { return std::isfinite(p) && p >= 0.0f && p <= 1.0f; }
@@ -184,6 +187,11 @@ static const char *check_config(const gsgp_config *cfg) {
     return "sigma_dtype must be GSGP_SIGMA_F32 or GSGP_SIGMA_BF16";
   if ((cfg->alloc == nullptr) != (cfg->free == nullptr))
     return "alloc and free must be given together";
+  if (cfg->init_mode != GSGP_INIT_RHH && cfg->init_mode != GSGP_INIT_LINEAR)
+    return "init_mode must be GSGP_INIT_RHH or GSGP_INIT_LINEAR";
+  if (cfg->init_mode == GSGP_INIT_LINEAR &&
+      (cfg->max_genes < 1 || cfg->max_genes > kMaxGenomeGenes))
+    return "max_genes must be in [1, 4095] for linear genomes";
   return nullptr;
 }
 
@@ -371,11 +379,13 @@ extern "C" gsgp_status gsgp_init(gsgp_ctx *c) {
   API_GUARD(c)
   if (c->state < 1) return fail(c, GSGP_E_STATE, "gsgp_init before gsgp_load");
   TRY(use_device(c));
+  c->state = 1;   // until this initialisation completes
   const gsgp_config &cf = c->cfg;
   const int m = cf.pop_size, r = cf.n_random_trees;
-  const int Kp = (1 << (cf.pop_max_depth + 1)) - 1;
-  const int Kr = (1 << (cf.rt_max_depth + 1)) - 1;
-  const int64_t key[7] = {m, r, c->n_pad, Kp, Kr, cf.sigma_dtype, 0};
+  const bool linear = cf.init_mode == GSGP_INIT_LINEAR;
+  const int Kp = linear ? cf.max_genes : (1 << (cf.pop_max_depth + 1)) - 1;
+  const int Kr = linear ? cf.max_genes : (1 << (cf.rt_max_depth + 1)) - 1;
+  const int64_t key[7] = {m, r, c->n_pad, Kp, Kr, cf.sigma_dtype, cf.init_mode};
   if (memcmp(key, c->layout_key, sizeof key) != 0) {
     free_run_buffers(c);
     c->Kp = Kp;
@@ -400,6 +410,7 @@ extern "C" gsgp_status gsgp_init(gsgp_ctx *c) {
     TRY(dalloc_n(c, &c->sel_ms, (size_t)m));
     TRY(dalloc_n(c, &c->dstate, 1));
     TRY(dalloc_n(c, &c->d_anc, 1));
+    TRY(dalloc_n(c, &c->d_stack, 2));
     memcpy(c->layout_key, key, sizeof key);
     c->graph_dirty = true;
     c->shape_ready = false;
@@ -408,14 +419,36 @@ extern "C" gsgp_status gsgp_init(gsgp_ctx *c) {
   c->model_gen = -1;
   TRY(ensure_trace(c, 64));
   const uint2 k2 = make_uint2((uint32_t)(cf.seed & 0xffffffffu), (uint32_t)(cf.seed >> 32));
-  LAUNCH(1, launch_treegen(m, cf.pop_min_depth, cf.pop_max_depth, Kp, c->l, k2, cf.run,
-                           kPurposePop, cf.p_grow_function, cf.p_feature_given_terminal,
-                           cf.const_lo, cf.const_hi, c->P_genes, c->P_consts, c->P_len,
-                           c->stream));
-  LAUNCH(1, launch_treegen(r, cf.rt_min_depth, cf.rt_max_depth, Kr, c->l, k2, cf.run,
-                           kPurposeRt, cf.p_grow_function, cf.p_feature_given_terminal,
-                           cf.const_lo, cf.const_hi, c->R_genes, c->R_consts, c->R_len,
-                           c->stream));
+  // interpreter stack entries below the top: a tree of depth d needs d + 1
+  int slots_p = cf.pop_max_depth + 1, slots_r = cf.rt_max_depth + 1;
+  if (linear) {
+    LAUNCH(1, launch_genomes(m, Kp, c->l, k2, cf.run, kPurposePop, cf.const_lo, cf.const_hi,
+                             c->P_genes, c->P_consts, c->P_len, c->stream));
+    LAUNCH(1, launch_genomes(r, Kr, c->l, k2, cf.run, kPurposeRt, cf.const_lo, cf.const_hi,
+                             c->R_genes, c->R_consts, c->R_len, c->stream));
+    // the deepest stack of each pool sizes the interpreter's stack
+    CK(cudaMemsetAsync(c->d_stack, 0, 2 * sizeof(int), c->stream));
+    LAUNCH(1, launch_max_stack(c->P_genes, c->P_len, m, Kp, c->d_stack, c->stream));
+    LAUNCH(1, launch_max_stack(c->R_genes, c->R_len, r, Kr, c->d_stack + 1, c->stream));
+    int h[2] = {0, 0};
+    CK(cudaMemcpyAsync(h, c->d_stack, sizeof h, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    if (h[0] > kMaxStack || h[1] > kMaxStack)
+      return fail(c, GSGP_E_INVALID,
+                  "a generated genome needs a stack of %d entries (limit %d); use a shorter "
+                  "max_genes or another seed", h[0] > h[1] ? h[0] : h[1], kMaxStack);
+    slots_p = h[0] > 1 ? h[0] : 1;
+    slots_r = h[1] > 1 ? h[1] : 1;
+  } else {
+    LAUNCH(1, launch_treegen(m, cf.pop_min_depth, cf.pop_max_depth, Kp, c->l, k2, cf.run,
+                             kPurposePop, cf.p_grow_function, cf.p_feature_given_terminal,
+                             cf.const_lo, cf.const_hi, c->P_genes, c->P_consts, c->P_len,
+                             c->stream));
+    LAUNCH(1, launch_treegen(r, cf.rt_min_depth, cf.rt_max_depth, Kr, c->l, k2, cf.run,
+                             kPurposeRt, cf.p_grow_function, cf.p_feature_given_terminal,
+                             cf.const_lo, cf.const_hi, c->R_genes, c->R_consts, c->R_len,
+                             c->stream));
+  }
   InterpParams ip{};
   ip.X = c->X;
   ip.target = c->t;
@@ -429,7 +462,7 @@ extern "C" gsgp_status gsgp_init(gsgp_ctx *c) {
   ip.consts = c->P_consts;
   ip.lengths = c->P_len;
   ip.K = Kp;
-  ip.stack_slots = cf.pop_max_depth + 1;
+  ip.stack_slots = slots_p;
   ip.out = c->pool;
   ip.partial = c->partial;
   LAUNCH(1, launch_interpret(0, ip, m, c->stream));
@@ -438,7 +471,7 @@ extern "C" gsgp_status gsgp_init(gsgp_ctx *c) {
   ip.consts = c->R_consts;
   ip.lengths = c->R_len;
   ip.K = Kr;
-  ip.stack_slots = cf.rt_max_depth + 1;
+  ip.stack_slots = slots_r;
   ip.out = c->sigR;
   ip.partial = nullptr;
   LAUNCH(1, launch_interpret(cf.sigma_dtype == GSGP_SIGMA_BF16 ? 2 : 1, ip, r, c->stream));
@@ -1050,8 +1083,11 @@ extern "C" gsgp_status gsgp_get_info(gsgp_ctx *c, gsgp_info *out) {
   out->n_cases_padded = c->n_pad;
   out->pop_size = c->cfg.pop_size;
   out->n_random_trees = c->cfg.n_random_trees;
-  out->pop_max_genes = (1 << (c->cfg.pop_max_depth + 1)) - 1;
-  out->rt_max_genes = (1 << (c->cfg.rt_max_depth + 1)) - 1;
+  // row lengths of the program arrays: the genome length for linear genomes,
+  // the full-tree size of the maximum depth for ramped half-and-half trees
+  const bool linear = c->cfg.init_mode == GSGP_INIT_LINEAR;
+  out->pop_max_genes = linear ? c->cfg.max_genes : (1 << (c->cfg.pop_max_depth + 1)) - 1;
+  out->rt_max_genes = linear ? c->cfg.max_genes : (1 << (c->cfg.rt_max_depth + 1)) - 1;
   out->generation = c->gen;
   out->evolve_tile_cases = c->shape_ready ? gen_tile_cases(c->shape) : 0;
   out->evolve_offspring_per_cta = c->shape_ready ? c->shape.opb : 0;

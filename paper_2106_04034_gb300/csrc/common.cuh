@@ -14,6 +14,8 @@ constexpr int kOpAdd = 0, kOpSub = 1, kOpMul = 2, kOpDiv = 3, kOpConst = 4, kOpV
 constexpr int kGenePad = -1;
 constexpr int kMaxDepth = 10;                    // deepest tree a pool may hold
 constexpr int kMaxGenes = (1 << (kMaxDepth + 1)) - 1;
+constexpr int kMaxGenomeGenes = 4095;             // longest linear genome
+constexpr int kMaxStack = 32;                     // deepest interpreter stack a program may use
 
 // Purposes of the initialisation streams (counter word 2 = 0x80000000 | p).
 constexpr uint32_t kInitFlag = 0x80000000u;

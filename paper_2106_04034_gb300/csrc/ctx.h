@@ -65,6 +65,7 @@ struct gsgp_ctx {
   int64_t lin_jump_cap = 0;
   int lin_start_cap = 0;
   int *d_anc = nullptr;
+  int *d_stack = nullptr;     // [2] deepest interpreter stack of P and R (linear genomes)
   unsigned *d_flag = nullptr;
   int gen = 0;
 

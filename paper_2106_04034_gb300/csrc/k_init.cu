@@ -88,6 +88,92 @@ cudaError_t launch_treegen(int count, int dmin, int dmax, int K, int n_features,
 }
 
 // ---------------------------------------------------------------------------
+// CreatePopulation in the paper's representation (Sec. 2.2,
+// "Initialization"): fixed-length linear genomes whose genes are drawn
+// independently, a function with weight 0.8, a feature 0.14, a constant
+// 0.04 (the printed probabilities, which add up to 0.98, as weights).  Gene j
+// of individual i reads words 2j (class, u24 against the two cumulative
+// thresholds) and 2j+1 (operator idx(w, 4), feature idx(w, l) or constant in
+// [lo, hi)) of the individual's stream; one thread makes the two genes of
+// one Philox block.
+// ---------------------------------------------------------------------------
+constexpr float kGenomePFunction = (float)(0.8 / 0.98);
+constexpr float kGenomePFunctionOrFeature = (float)((0.8 + 0.14) / 0.98);
+
+__global__ void __launch_bounds__(256)
+    genome_kernel(int count, int K, int n_features, uint2 key, uint32_t run, uint32_t purpose,
+                  float lo, float hi, int *__restrict__ genes, float *__restrict__ consts,
+                  int *__restrict__ lengths) {
+  const int pairs = (K + 1) / 2;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (int64_t)count * pairs) return;
+  const int i = (int)(t / pairs);
+  const int q = (int)(t - (int64_t)i * pairs);
+  const uint4 w = philox4x32_10(make_uint4((uint32_t)q, (uint32_t)i, kInitFlag | purpose, run), key);
+  const uint32_t words[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int j = 2 * q + h;
+    if (j >= K) break;
+    const float u = draw_u24(words[2 * h]);
+    const uint32_t c = words[2 * h + 1];
+    int g;
+    float v = 0.0f;
+    if (u < kGenomePFunction) {
+      g = (int)draw_index(c, 4u);
+    } else if (u < kGenomePFunctionOrFeature) {
+      g = kOpVar | ((int)draw_index(c, (uint32_t)n_features) << 8);
+    } else {
+      g = kOpConst;
+      v = draw_const(c, lo, hi);
+    }
+    genes[(size_t)i * K + j] = g;
+    consts[(size_t)i * K + j] = v;
+  }
+  if (q == 0) lengths[i] = K;
+}
+
+cudaError_t launch_genomes(int count, int K, int n_features, uint2 key, uint32_t run,
+                           uint32_t purpose, float const_lo, float const_hi, int *genes,
+                           float *consts, int *lengths, cudaStream_t s) {
+  if (count <= 0) return cudaSuccess;
+  const int64_t threads = (int64_t)count * ((K + 1) / 2);
+  genome_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(
+      count, K, n_features, key, run, purpose, const_lo, const_hi, genes, consts, lengths);
+  return cudaGetLastError();
+}
+
+// Deepest stack any program of a pool reaches under the interpreter's rule
+// (a function short of operands is skipped): sizes the interpreter's shared
+// memory stack.  One thread per program; *out must be zero before.
+__global__ void __launch_bounds__(256)
+    max_stack_kernel(const int *__restrict__ genes, const int *__restrict__ lengths, int count,
+                     int K, int *__restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= count) return;
+  const int *g = genes + (size_t)i * K;
+  const int len = lengths[i];
+  int sp = 0, best = 0;
+  for (int k = 0; k < len; ++k) {
+    const int op = g[k] & 0xFF;
+    if (op >= kOpConst) {
+      ++sp;
+      best = max(best, sp);
+    } else if (sp >= 2) {
+      --sp;
+    }
+  }
+  atomicMax(out, best);
+}
+
+cudaError_t launch_max_stack(const int *genes, const int *lengths, int count, int K, int *out,
+                             cudaStream_t s) {
+  if (count <= 0) return cudaSuccess;
+  max_stack_kernel<<<(count + 255) / 256, 256, 0, s>>>(genes, lengths, count, K, out);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
 // Row-major cases (n x l) -> feature-major X[f][col0 + j] through a padded
 // 32 x 32 shared tile, so both the reads and the writes are coalesced.
 // ---------------------------------------------------------------------------
@@ -141,8 +227,9 @@ cudaError_t launch_nonfinite_check(const float *v, int64_t n, unsigned *flag, cu
 // row), so the gene stream is uniform across the CTA and decoded once per
 // 4 cases.  The top of the stack lives in registers; deeper entries live in
 // shared memory laid out [slot][thread] (conflict-free 16-byte accesses).
-// A function with fewer than two operands on the stack is skipped (the
-// paper's rule; generated programs never trigger it).  Protected division
+// A function with fewer than two operands on the stack is skipped and the
+// value is register Out, the last function output (the paper's rules; a
+// ramped half-and-half program never skips and ends with its root).  Protected division
 // returns 1 when |b| < eps.  Random trees are wrapped by the logistic
 // function (Sec. 2) and stored as float or bf16.  For the population the
 // CTA also reduces the squared errors of its tile (train and test cases) in
@@ -184,6 +271,8 @@ __global__ void __launch_bounds__(kInterpThreads) interpret_kernel(InterpParams 
   const bool valid = j4 * 4 < p.n_pad;
   const int64_t jj = valid ? j4 : 0;
   float4 tos = make_float4(0.f, 0.f, 0.f, 0.f);
+  float4 out = tos;        // register Out: the last function output
+  bool applied = false;    // uniform across the CTA (depends on the genes only)
   int sp = 0;
   for (int k = 0; k < len; ++k) {
     const int g = s_gene[k];
@@ -206,8 +295,14 @@ __global__ void __launch_bounds__(kInterpThreads) interpret_kernel(InterpParams 
       tos.z = apply_op(op, a.z, tos.z, p.protect_eps);
       tos.w = apply_op(op, a.w, tos.w, p.protect_eps);
       --sp;
+      out = tos;
+      applied = true;
     }
   }
+  // the program's value is Out (Sec. 2.2, "Interpreter"); a program that
+  // applies no function gives its stack top (0 when empty).  For a
+  // well-formed postfix program Out is the final stack top.
+  if (applied) tos = out;
 
   if (MODE == 0) {
     float str = 0.f, ste = 0.f;

@@ -79,68 +79,55 @@ cudaError_t launch_lineage(const int4 *trace, int m, int G, const DevState *stat
   return cudaGetLastError();
 }
 
-// Float64 postfix evaluation of one program on case j (protected division:
-// |b| < eps gives 1; a function short of operands is skipped).
-__device__ double eval_program64(const int *__restrict__ genes, const float *__restrict__ consts,
-                                 int len, const float *__restrict__ X, int64_t n_pad, int64_t j,
-                                 double eps) {
-  double st[kMaxDepth + 2];
+// Evaluation of one program on case j with the interpreter's rules: a
+// function short of operands is skipped, the value is register Out (the last
+// function output), else the stack top, else 0.  Programs are checked at
+// initialisation to need at most kMaxStack stack entries.
+template <typename T>
+__device__ __forceinline__ T eval_program(const int *__restrict__ genes,
+                                          const float *__restrict__ consts, int len,
+                                          const float *__restrict__ X, int64_t n_pad, int64_t j,
+                                          T eps) {
+  T st[kMaxStack];
+  T out = T(0);
+  bool applied = false;
   int sp = 0;
   for (int k = 0; k < len; ++k) {
     const int g = genes[k];
     const int op = g & 0xFF;
     if (op == kOpVar) {
-      if (sp < kMaxDepth + 2) st[sp++] = (double)X[(int64_t)(g >> 8) * n_pad + j];
+      if (sp < kMaxStack) st[sp++] = (T)X[(int64_t)(g >> 8) * n_pad + j];
     } else if (op == kOpConst) {
-      if (sp < kMaxDepth + 2) st[sp++] = (double)consts[k];
+      if (sp < kMaxStack) st[sp++] = (T)consts[k];
     } else if (sp >= 2) {
-      const double b = st[sp - 1];
-      const double a = st[sp - 2];
-      double r;
+      const T b = st[sp - 1];
+      const T a = st[sp - 2];
+      T r;
       switch (op) {
         case kOpAdd: r = a + b; break;
         case kOpSub: r = a - b; break;
         case kOpMul: r = a * b; break;
-        default: r = fabs(b) < eps ? 1.0 : a / b; break;
+        default: r = fabs(b) < eps ? T(1) : a / b; break;
       }
       st[sp - 2] = r;
       --sp;
+      out = r;
+      applied = true;
     }
   }
-  return sp ? st[sp - 1] : 0.0;
+  return applied ? out : (sp ? st[sp - 1] : T(0));
 }
 
-// Float32 evaluation of one program on case j with the interpreter's
-// arithmetic (one rounding per operation, protected division on the float
-// divisor), so that sigma of a random tree comes out bit-identical to the
-// value the interpreter stored during initialisation.
-__device__ float eval_program32(const int *__restrict__ genes, const float *__restrict__ consts,
-                                int len, const float *__restrict__ X, int64_t n_pad, int64_t j,
-                                float eps) {
-  float st[kMaxDepth + 2];
-  int sp = 0;
-  for (int k = 0; k < len; ++k) {
-    const int g = genes[k];
-    const int op = g & 0xFF;
-    if (op == kOpVar) {
-      if (sp < kMaxDepth + 2) st[sp++] = X[(int64_t)(g >> 8) * n_pad + j];
-    } else if (op == kOpConst) {
-      if (sp < kMaxDepth + 2) st[sp++] = consts[k];
-    } else if (sp >= 2) {
-      const float b = st[sp - 1];
-      const float a = st[sp - 2];
-      float r;
-      switch (op) {
-        case kOpAdd: r = a + b; break;
-        case kOpSub: r = a - b; break;
-        case kOpMul: r = a * b; break;
-        default: r = fabsf(b) < eps ? 1.0f : a / b; break;
-      }
-      st[sp - 2] = r;
-      --sp;
-    }
-  }
-  return sp ? st[sp - 1] : 0.0f;
+// float64: the model's arithmetic.  float32: the interpreter's arithmetic
+// (one rounding per operation, protected division on the float divisor), so
+// that sigma of a random tree comes out bit-identical to the stored value.
+__device__ double eval_program64(const int *genes, const float *consts, int len, const float *X,
+                                 int64_t n_pad, int64_t j, double eps) {
+  return eval_program<double>(genes, consts, len, X, n_pad, j, eps);
+}
+__device__ float eval_program32(const int *genes, const float *consts, int len, const float *X,
+                                int64_t n_pad, int64_t j, float eps) {
+  return eval_program<float>(genes, consts, len, X, n_pad, j, eps);
 }
 
 // y(x) = ancestor(x) + sum_k coef_k * q(sigma(R_k(x))) in float64.  With

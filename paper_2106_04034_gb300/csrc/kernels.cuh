@@ -13,6 +13,14 @@ cudaError_t launch_treegen(int count, int dmin, int dmax, int K, int n_features,
                            float const_lo, float const_hi, int *genes, float *consts,
                            int *lengths, cudaStream_t s);
 
+// The paper's linear genomes (fixed length K) for a pool, and the deepest
+// stack any program of a pool reaches (atomicMax into *out).
+cudaError_t launch_genomes(int count, int K, int n_features, uint2 key, uint32_t run,
+                           uint32_t purpose, float const_lo, float const_hi, int *genes,
+                           float *consts, int *lengths, cudaStream_t s);
+cudaError_t launch_max_stack(const int *genes, const int *lengths, int count, int K, int *out,
+                             cudaStream_t s);
+
 cudaError_t launch_transpose(const float *in, int64_t n, int l, float *out, int64_t n_pad,
                              int64_t col0, cudaStream_t s);
 

@@ -18,7 +18,7 @@ def oracle_params(w: W.Workload, **over) -> og.Params:
                   pop_max_depth=w.pop_max_depth, rt_min_depth=w.rt_min_depth,
                   rt_max_depth=w.rt_max_depth, const_lo=w.const_lo, const_hi=w.const_hi,
                   protect_eps=w.protect_eps, ms=w.ms, tournament_size=w.tournament_size,
-                  sigma_bf16=w.sigma_bf16)
+                  sigma_bf16=w.sigma_bf16, init_mode=w.init_mode, max_genes=w.max_genes)
     for k, v in over.items():
         setattr(p, k, v)
     return p
@@ -36,7 +36,8 @@ def gpu_run(w: W.Workload, data=None, **over):
         const_hi=p.const_hi, protect_eps=p.protect_eps, ms=p.ms, ms_mode=p.ms_mode,
         tournament_size=p.tournament_size, elitism=int(p.elitism),
         p_grow_function=p.p_grow, p_feature_given_terminal=p.p_feature,
-        sigma_dtype=pkg.SIGMA_BF16 if p.sigma_bf16 else pkg.SIGMA_F32)
+        sigma_dtype=pkg.SIGMA_BF16 if p.sigma_bf16 else pkg.SIGMA_F32,
+        init_mode=p.init_mode, max_genes=p.max_genes)
     cfg.stream = torch.cuda.current_stream().cuda_stream
     run = pkg.Run(cfg)
     if data is None:
@@ -63,12 +64,12 @@ def semantics_close(gpu, ref, bound=None):
     return ok, by_bound.mean(), ambiguous.mean()
 
 
-def oracle_semantics_with_bounds(P, X, eps, logistic=False):
+def oracle_semantics_with_bounds(P, X, eps, logistic=False, linear=False):
     genes, consts, lengths = P
     vals, bounds = [], []
     for i in range(genes.shape[0]):
         L = int(lengths[i])
-        v, e = oi.eval_postfix_fp32_bound(genes[i, :L], consts[i, :L], X, eps)
+        v, e = oi.eval_postfix_fp32_bound(genes[i, :L], consts[i, :L], X, eps, linear=linear)
         if logistic:
             v = oi.sigma(v)
             e = oi.sigma_fp32_bound(e)

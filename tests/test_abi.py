@@ -165,3 +165,18 @@ def test_batch_arguments_and_state_without_device(lib):
     lib.gsgp_batch_destroy(None)
     for r in runs:
         r.close()
+
+
+def test_linear_genome_config_checks(lib):
+    cfg = pkg.default_config()
+    assert (cfg.init_mode, cfg.max_genes) == (pkg.INIT_RHH, 127)
+    for mode, k, ok in ((pkg.INIT_LINEAR, 127, True), (pkg.INIT_LINEAR, 4095, True),
+                        (pkg.INIT_LINEAR, 0, False), (pkg.INIT_LINEAR, 4096, False),
+                        (2, 127, False), (pkg.INIT_RHH, 0, True)):
+        cfg = pkg.default_config(init_mode=mode, max_genes=k)
+        assert (lib.gsgp_config_error(C.byref(cfg)) == b"") == ok, (mode, k)
+    # depths are not checked for linear genomes' programs, but stay valid fields
+    cfg = pkg.default_config(init_mode=pkg.INIT_LINEAR, max_genes=2047)
+    r = pkg.Run(cfg)
+    assert r.info().pop_max_genes == 2047 and r.info().rt_max_genes == 2047
+    r.close()

@@ -49,6 +49,8 @@ class Workload:
     target: str = "poly"            # "poly" | "tree5" | "monomials" | "tree4"
     noise: float = 0.0              # standard deviation of the additive noise
     wid: int = 0                    # workload id, mixed into the data seed
+    init_mode: int = 0              # 0 ramped half-and-half trees, 1 linear genomes
+    max_genes: int = 127            # genome length (init_mode 1)
 
     @property
     def n_cases(self) -> int:
