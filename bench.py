@@ -71,6 +71,17 @@ def job_value(units_per_rank: float, world: int, seconds: float) -> float:
     return units_per_rank * world / seconds
 
 
+def alu_peak_tops():
+    """FP32 lane operations per second of the GPU (T/s): 152 SMs x 128 lanes
+    x the maximum SM clock from MEASURED_PEAKS.json (2070 MHz if absent)."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            mhz = float(json.load(fh)["sm_max_mhz"])
+    except Exception:
+        mhz = 2070.0
+    return 152 * 128 * mhz * 1e6 / 1e12
+
+
 def profiled_traffic(workload_name: str):
     """DRAM bytes per generation of the generation kernel from the committed
     ncu summary, if it was taken on this workload with the current kernel
@@ -182,15 +193,7 @@ def run_ours(args, rank, world, local_rank):
     Xtr, ytr, Xte, yte = data
     dev = [torch.from_numpy(a).cuda() for a in data]
     stream = torch.cuda.current_stream()
-    cfg = pkg.default_config(
-        seed=w.seed, run=w.run, pop_size=w.pop_size, n_random_trees=w.n_random_trees,
-        pop_min_depth=w.pop_min_depth, pop_max_depth=w.pop_max_depth,
-        rt_min_depth=w.rt_min_depth, rt_max_depth=w.rt_max_depth, ms=w.ms,
-        tournament_size=w.tournament_size, const_lo=w.const_lo, const_hi=w.const_hi,
-        protect_eps=w.protect_eps,
-        sigma_dtype=pkg.SIGMA_BF16 if w.sigma_bf16 else pkg.SIGMA_F32)
-    cfg.stream = stream.cuda_stream
-    run = pkg.Run(cfg)
+    run = pkg.Run(make_config(pkg, w, stream))
     if args.shape:
         vec, opb = (int(v) for v in args.shape.split(","))
         run.set_evolve_shape(pkg.PATH_PERSISTENT, vec, opb)
@@ -225,6 +228,7 @@ def run_ours(args, rank, world, local_rank):
     barrier()
     clock = clocks.stop()
     kernel_ms = [run.kernel_times(1 << 22)]
+    interp_ms = run.init_kernel_times()          # the last step's two interpreter launches
     launches = run.info().kernel_launches - launches0
     ms_total = e0.elapsed_time(e1)
     run.set_kernel_timing(False)
@@ -252,6 +256,34 @@ def run_ours(args, rank, world, local_rank):
     peak, peak_kind = measured_peak_gbs()
     per_gen_traffic = profiled_traffic(w.name)
     traffic = None if per_gen_traffic is None else per_gen_traffic * G / per_launch.size
+    stream_roofline = {
+        "kernel": kname, "bound": "hbm", "achieved": achieved, "peak": peak,
+        "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
+        "algorithmic_bytes_per_launch": avg_bytes, "avg_launch_ms": avg_ms,
+        "launches_timed": int(kms.size), "generations_per_launch": per,
+        "shape": {"path": "persistent" if info.evolve_path == 1 else "chained",
+                  "tile_cases": info.evolve_tile_cases,
+                  "offspring_per_cta": info.evolve_offspring_per_cta,
+                  "grid": info.evolve_grid}}
+
+    # the interpreter (ComputeSemantics of P and R): one gene applied to one
+    # case is the unit of work, one lane operation at the least, against the
+    # FP32 lanes' issue rate (152 SMs x 128 lanes x clock)
+    gene_cases = [float(run.programs(pool)[2].sum()) * w.n_cases
+                  for pool in (pkg.POOL_POPULATION, pkg.POOL_RANDOM)]
+    interp_s = float(interp_ms.sum()) / 1e3
+    alu_peak = alu_peak_tops()
+    interp_tops = sum(gene_cases) / interp_s / 1e12
+    interp_roofline = {
+        "kernel": "interpret_kernel", "bound": "alu", "achieved": interp_tops,
+        "peak": alu_peak, "peak_kind": "derived: 152 SMs x 128 FP32 lanes x max SM clock",
+        "unit": "T lane-ops/s (1 per gene per case)", "frac": interp_tops / alu_peak,
+        "traffic": None, "gene_cases_per_init": sum(gene_cases),
+        "launch_ms": [float(v) for v in interp_ms]}
+    # the dominant kernel of a step carries the headline roofline
+    stream_ms_step = float(kms.sum()) / args.steps
+    roofline = interp_roofline if float(interp_ms.sum()) > stream_ms_step else stream_roofline
+    secondary = stream_roofline if roofline is interp_roofline else interp_roofline
 
     # end to end through host buffers: host->device copies of the cases,
     # the whole run, prediction copied back to the host
@@ -285,20 +317,15 @@ def run_ours(args, rank, world, local_rank):
                    "n_train": w.n_train, "n_test": w.n_test, "generations": G,
                    "tournament_size": w.tournament_size, "ms": w.ms,
                    "sigma": "bf16" if w.sigma_bf16 else "f32",
+                   "programs": (f"linear genomes of {w.max_genes} genes" if w.init_mode == 1
+                                else f"ramped half-and-half trees, depth {w.pop_min_depth}-"
+                                     f"{w.pop_max_depth}"),
                    "parallelism": f"replicas x{world}",
                    "l2": "working set larger than L2 (semantic matrices %.0f MB)"
                          % ((2 * w.pop_size + w.n_random_trees) * w.n_cases * 4 / 1e6),
                    "step": "load_device + init + evolve(G) + best_trace + predict(test)"},
-        "roofline": {"kernel": kname, "bound": "hbm", "achieved": achieved,
-                     "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": traffic,
-                     "algorithmic_bytes_per_launch": avg_bytes,
-                     "avg_launch_ms": avg_ms, "launches_timed": int(kms.size),
-                     "generations_per_launch": per,
-                     "shape": {"path": "persistent" if info.evolve_path == 1 else "chained",
-                               "tile_cases": info.evolve_tile_cases,
-                               "offspring_per_cta": info.evolve_offspring_per_cta,
-                               "grid": info.evolve_grid}},
+        "roofline": roofline,
+        "roofline_other": secondary,
         "e2e": {"value": job_value(updates, world, e2e_s), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h)},
         "gpu_launches": int(launches),
@@ -315,7 +342,8 @@ def make_config(pkg, w: W.Workload, stream):
         rt_min_depth=w.rt_min_depth, rt_max_depth=w.rt_max_depth, ms=w.ms,
         tournament_size=w.tournament_size, const_lo=w.const_lo, const_hi=w.const_hi,
         protect_eps=w.protect_eps,
-        sigma_dtype=pkg.SIGMA_BF16 if w.sigma_bf16 else pkg.SIGMA_F32)
+        sigma_dtype=pkg.SIGMA_BF16 if w.sigma_bf16 else pkg.SIGMA_F32,
+        init_mode=w.init_mode, max_genes=w.max_genes)
     cfg.stream = stream.cuda_stream
     return cfg
 
@@ -484,14 +512,20 @@ def run_batched(args, rank, world, local_rank):
 
 def cpu_baseline(w: W.Workload, target_s: float = 12.0, max_gens: int = 200):
     """The float64 oracle, as it stands, on the host cores: generations of the
-    same workload until about target_s seconds of evolution were timed."""
+    same workload until about target_s seconds of evolution were timed.  On
+    workloads whose initialisation would take the oracle many minutes the
+    sample keeps every case but at most 128 programs per pool."""
     from oracle import gsgp as og
+    full_m = w.pop_size
+    big = w.pop_size * w.n_cases * w.max_genes > 2e10 if w.init_mode == 1 else False
+    if big:
+        w = w.replace(pop_size=min(w.pop_size, 128), n_random_trees=min(w.n_random_trees, 128))
     p = og.Params(seed=w.seed, run=w.run, pop_size=w.pop_size,
                   n_random_trees=w.n_random_trees, pop_min_depth=w.pop_min_depth,
                   pop_max_depth=w.pop_max_depth, rt_min_depth=w.rt_min_depth,
                   rt_max_depth=w.rt_max_depth, ms=w.ms, tournament_size=w.tournament_size,
                   const_lo=w.const_lo, const_hi=w.const_hi, protect_eps=w.protect_eps,
-                  sigma_bf16=w.sigma_bf16)
+                  sigma_bf16=w.sigma_bf16, init_mode=w.init_mode, max_genes=w.max_genes)
     o = og.GSGP(p, *W.make_data(w))
     o.init()
     t0 = time.perf_counter()
@@ -500,10 +534,11 @@ def cpu_baseline(w: W.Workload, target_s: float = 12.0, max_gens: int = 200):
         o.generation()
         gens += 1
     dt = time.perf_counter() - t0
+    shrunk = f", m and r cut from {full_m} to {w.pop_size}" if big else ""
     return {"value": w.pop_size * w.n_cases * gens / dt, "unit": UNIT, "cores": 1,
             "kind": "oracle",
             "sample": f"{gens} generations of the {w.name.split(':')[0]} workload "
-                      f"(full n_cases={w.n_cases}, m={w.pop_size}) after an untimed init; "
+                      f"(full n_cases={w.n_cases}{shrunk}) after an untimed init; "
                       f"float64 numpy, single thread, {os.cpu_count()} host cores present"}
 
 

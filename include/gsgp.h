@@ -303,6 +303,13 @@ gsgp_status gsgp_set_evolve_shape(gsgp_ctx *ctx, int32_t path, int32_t vec, int3
 gsgp_status gsgp_set_kernel_timing(gsgp_ctx *ctx, int32_t enabled);
 gsgp_status gsgp_kernel_times(gsgp_ctx *ctx, float *ms, int32_t cap, int32_t *n_out);
 
+/* With kernel timing enabled, gsgp_init also records events around its two
+ * interpreter launches (ComputeSemantics of P, then of R);
+ * gsgp_init_kernel_times synchronises and writes their durations in ms to
+ * HOST ms[0], ms[1].  Errors: GSGP_E_STATE (the last init was not timed),
+ * GSGP_E_INVALID. */
+gsgp_status gsgp_init_kernel_times(gsgp_ctx *ctx, float *ms);
+
 /* Philox4x32-10 words [0, n_words) of the stream (individual,
  * gen_or_purpose, run) under key `seed`, computed on the GPU on `stream` and
  * copied to HOST `out`.  Errors: GSGP_E_INVALID, GSGP_E_CUDA. */

@@ -112,6 +112,7 @@ _SIGS = {
     "gsgp_set_evolve_shape": (C.c_int, [P, C.c_int32, C.c_int32, C.c_int32]),
     "gsgp_set_kernel_timing": (C.c_int, [P, C.c_int32]),
     "gsgp_kernel_times": (C.c_int, [P, P, C.c_int32, P]),
+    "gsgp_init_kernel_times": (C.c_int, [P, P]),
     "gsgp_rng_words": (C.c_int, [C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint32, C.c_int32, P, P]),
     "gsgp_mutate_noalloc": (C.c_int, [P, P, C.c_int64, P, C.c_int64, C.c_int64, P, P, P, P,
                                       C.c_int32, P, P, P, P, C.c_char_p, C.c_size_t]),
@@ -365,6 +366,12 @@ class Run:
         n = C.c_int32(0)
         self._check(self.lib.gsgp_kernel_times(self.ctx, _ptr(out), cap, C.byref(n)))
         return out[:n.value].copy()
+
+    def init_kernel_times(self) -> np.ndarray:
+        """ms of the last init's two interpreter launches (population, random trees)."""
+        out = np.zeros(2, np.float32)
+        self._check(self.lib.gsgp_init_kernel_times(self.ctx, _ptr(out)))
+        return out
 
 
 class Batch:

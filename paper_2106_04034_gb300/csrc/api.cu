@@ -465,7 +465,12 @@ extern "C" gsgp_status gsgp_init(gsgp_ctx *c) {
   ip.stack_slots = slots_p;
   ip.out = c->pool;
   ip.partial = c->partial;
+  c->init_timed = false;
+  if (c->timing && !c->ev_init[0])
+    for (auto &e : c->ev_init) CK(cudaEventCreate(&e));
+  if (c->timing) CK(cudaEventRecord(c->ev_init[0], c->stream));
   LAUNCH(1, launch_interpret(0, ip, m, c->stream));
+  if (c->timing) CK(cudaEventRecord(c->ev_init[1], c->stream));
   // random-tree semantics wrapped by the logistic function
   ip.genes = c->R_genes;
   ip.consts = c->R_consts;
@@ -474,7 +479,12 @@ extern "C" gsgp_status gsgp_init(gsgp_ctx *c) {
   ip.stack_slots = slots_r;
   ip.out = c->sigR;
   ip.partial = nullptr;
+  if (c->timing) CK(cudaEventRecord(c->ev_init[2], c->stream));
   LAUNCH(1, launch_interpret(cf.sigma_dtype == GSGP_SIGMA_BF16 ? 2 : 1, ip, r, c->stream));
+  if (c->timing) {
+    CK(cudaEventRecord(c->ev_init[3], c->stream));
+    c->init_timed = true;
+  }
   LAUNCH(1, launch_fitness_finalize(c->partial, c->tiles_interp, m, (int)c->n_tr, (int)c->n_te,
                                     c->fit, c->fit_te, c->stream));
   LAUNCH(1, launch_init_state(m, c->perm, c->fit, c->dstate, c->stream));
@@ -1235,6 +1245,19 @@ extern "C" gsgp_status gsgp_kernel_times(gsgp_ctx *c, float *ms, int32_t cap, in
   API_END(c)
 }
 
+extern "C" gsgp_status gsgp_init_kernel_times(gsgp_ctx *c, float *ms) {
+  API_GUARD(c)
+  if (!ms) return fail(c, GSGP_E_INVALID, "ms must hold 2 floats");
+  if (!c->init_timed)
+    return fail(c, GSGP_E_STATE, "the last gsgp_init ran without kernel timing");
+  TRY(use_device(c));
+  CK(cudaEventSynchronize(c->ev_init[3]));
+  CK(cudaEventElapsedTime(&ms[0], c->ev_init[0], c->ev_init[1]));
+  CK(cudaEventElapsedTime(&ms[1], c->ev_init[2], c->ev_init[3]));
+  return GSGP_OK;
+  API_END(c)
+}
+
 extern "C" gsgp_status gsgp_rng_words(uint64_t seed, uint32_t run, uint32_t gp,
                                       uint32_t individual, int32_t n_words, uint32_t *out,
                                       void *stream) {
@@ -1272,6 +1295,8 @@ extern "C" void gsgp_destroy(gsgp_ctx *c) {
     for (auto e : c->ev0) cudaEventDestroy(e);
     for (auto e : c->ev_marks) cudaEventDestroy(e);
     for (auto e : c->ev1) cudaEventDestroy(e);
+    for (auto e : c->ev_init)
+      if (e) cudaEventDestroy(e);
     cudaStreamSynchronize(c->stream);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     cudaGetLastError();

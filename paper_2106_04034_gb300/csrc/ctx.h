@@ -82,6 +82,8 @@ struct gsgp_ctx {
   // stream-kernel timing
   bool timing = false;
   std::vector<cudaEvent_t> ev0, ev1;
+  cudaEvent_t ev_init[4] = {nullptr, nullptr, nullptr, nullptr};   // around the interpreter
+  bool init_timed = false;                                          // launches of the last init
   int ev_used = 0;
 
   // rebuilt best model (valid while model_gen == gen)

@@ -86,7 +86,25 @@ LARGE_BF16 = LARGE.replace(
     name="large-bf16: LARGE with sigma(R) stored bf16, G=2000",
     generations=2000, sigma_bf16=True)
 
-WORKLOADS = {"tiny": TINY, "mid": MID, "large": LARGE, "large_bf16": LARGE_BF16}
+# The shape of the paper's speed-up measurements (Sec. 3, "dummy datasets"):
+# n = 102,400 cases, l = 1,024 features, m = 10,240, 50 generations, linear
+# genomes of k in {127, 1023, 2047} genes.  The paper does not state the
+# number of random trees; r = m here.  The train/test split and the target
+# are this build's (the paper's dummy data is unspecified).
+PAPER_K127 = Workload(
+    name="paper k=127: l=1024 U[-1,1], n=81920+20480, m=10240, r=10240, linear genomes, G=50",
+    n_features=1024, n_train=81920, n_test=20480, pop_size=10240, n_random_trees=10240,
+    pop_min_depth=2, pop_max_depth=6, rt_min_depth=2, rt_max_depth=6, generations=50,
+    target="tree5", noise=0.05, wid=5, init_mode=1, max_genes=127)
+PAPER_K1023 = PAPER_K127.replace(
+    name="paper k=1023: l=1024 U[-1,1], n=81920+20480, m=10240, r=10240, linear genomes, G=50",
+    max_genes=1023)
+PAPER_K2047 = PAPER_K127.replace(
+    name="paper k=2047: l=1024 U[-1,1], n=81920+20480, m=10240, r=10240, linear genomes, G=50",
+    max_genes=2047)
+
+WORKLOADS = {"tiny": TINY, "mid": MID, "large": LARGE, "large_bf16": LARGE_BF16,
+             "paper_k127": PAPER_K127, "paper_k1023": PAPER_K1023, "paper_k2047": PAPER_K2047}
 
 
 def _rng(w: Workload, salt: int = 0) -> np.random.Generator:
