@@ -187,6 +187,9 @@ def run_ours(args, rank, world, local_rank):
     w = W.WORKLOADS[args.workload]
     if args.generations:
         w = w.replace(generations=args.generations)
+    if args.pop_size:     # smaller pools of the same shape, e.g. for ncu captures
+        w = w.replace(pop_size=args.pop_size, n_random_trees=args.pop_size,
+                      name=f"{w.name.split(':')[0]} with m = r = {args.pop_size}")
     w = replica_workload(w, rank)
     G = w.generations
     data = W.make_data(w)
@@ -269,16 +272,20 @@ def run_ours(args, rank, world, local_rank):
     # the interpreter (ComputeSemantics of P and R): one gene applied to one
     # case is the unit of work, one lane operation at the least, against the
     # FP32 lanes' issue rate (152 SMs x 128 lanes x clock)
-    gene_cases = [float(run.programs(pool)[2].sum()) * w.n_cases
-                  for pool in (pkg.POOL_POPULATION, pkg.POOL_RANDOM)]
+    # (the evaluated genes: for linear genomes the live code, see DESIGN)
+    info_i = run.info()
+    gene_cases = float(info_i.pop_evaluated_genes + info_i.rt_evaluated_genes) * w.n_cases
+    genome_cases = float(sum(run.programs(pool)[2].sum()
+                             for pool in (pkg.POOL_POPULATION, pkg.POOL_RANDOM))) * w.n_cases
     interp_s = float(interp_ms.sum()) / 1e3
     alu_peak = alu_peak_tops()
-    interp_tops = sum(gene_cases) / interp_s / 1e12
+    interp_tops = gene_cases / interp_s / 1e12
     interp_roofline = {
         "kernel": "interpret_kernel", "bound": "alu", "achieved": interp_tops,
         "peak": alu_peak, "peak_kind": "derived: 152 SMs x 128 FP32 lanes x max SM clock",
-        "unit": "T lane-ops/s (1 per gene per case)", "frac": interp_tops / alu_peak,
-        "traffic": None, "gene_cases_per_init": sum(gene_cases),
+        "unit": "T lane-ops/s (1 per evaluated gene per case)", "frac": interp_tops / alu_peak,
+        "traffic": None, "evaluated_gene_cases_per_init": gene_cases,
+        "genome_gene_cases_per_init": genome_cases,
         "launch_ms": [float(v) for v in interp_ms]}
     # the dominant kernel of a step carries the headline roofline
     stream_ms_step = float(kms.sum()) / args.steps
@@ -596,6 +603,8 @@ def main():
     ap.add_argument("--generations", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-gens-per-step", type=int, default=3)
+    ap.add_argument("--pop-size", type=int, default=0,
+                    help="m = r override (smaller cases of a workload, e.g. for ncu captures)")
     ap.add_argument("--shape", default="",
                     help="vec,opb of the mutation stream instead of autotuning (e.g. 2,4)")
     ap.add_argument("--batch-runs", type=int, default=BATCH_RUNS,

@@ -245,6 +245,8 @@ typedef struct {
   int32_t evolve_generations_per_launch;
   int64_t kernel_launches;            /* library kernels launched since create */
   int64_t device_bytes;               /* device memory held by the context */
+  int64_t pop_evaluated_genes;        /* genes the interpreter applies per case over P and R: */
+  int64_t rt_evaluated_genes;         /* the live code of linear genomes, else all genes */
 } gsgp_info;
 
 gsgp_status gsgp_get_info(gsgp_ctx *ctx, gsgp_info *out);

@@ -77,6 +77,7 @@ class Info(C.Structure):
         ("evolve_path", C.c_int32), ("evolve_grid", C.c_int32),
         ("evolve_generations_per_launch", C.c_int32),
         ("kernel_launches", C.c_int64), ("device_bytes", C.c_int64),
+        ("pop_evaluated_genes", C.c_int64), ("rt_evaluated_genes", C.c_int64),
     ]
 
 

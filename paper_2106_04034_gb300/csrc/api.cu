@@ -87,6 +87,14 @@ static void free_run_buffers(gsgp_ctx *c) {
   dfree(c, c->R_genes);
   dfree(c, c->R_consts);
   dfree(c, c->R_len);
+  if (c->Pc_genes) {   // owned only for linear genomes; otherwise aliases
+    dfree(c, c->Pc_genes);
+    dfree(c, c->Pc_consts);
+    dfree(c, c->Pc_len);
+    dfree(c, c->Rc_genes);
+    dfree(c, c->Rc_consts);
+    dfree(c, c->Rc_len);
+  }
   dfree(c, c->pool);
   dfree(c, c->sigR);
   dfree(c, c->perm);
@@ -322,6 +330,20 @@ extern "C" gsgp_status gsgp_load_device(gsgp_ctx *c, const float *Xtr, const flo
 }
 
 // ------------------------------------------------------------------ init --
+// Programs as evaluated: the live code of linear genomes, else the programs.
+static const int *prog_genes(const gsgp_ctx *c, bool pop) {
+  if (c->Pc_genes) return pop ? c->Pc_genes : c->Rc_genes;
+  return pop ? c->P_genes : c->R_genes;
+}
+static const float *prog_consts(const gsgp_ctx *c, bool pop) {
+  if (c->Pc_genes) return pop ? c->Pc_consts : c->Rc_consts;
+  return pop ? c->P_consts : c->R_consts;
+}
+static const int *prog_len(const gsgp_ctx *c, bool pop) {
+  if (c->Pc_genes) return pop ? c->Pc_len : c->Rc_len;
+  return pop ? c->P_len : c->R_len;
+}
+
 GenParams gen_params(gsgp_ctx *c) {
   GenParams p{};
   p.target = c->t;
@@ -399,6 +421,14 @@ extern "C" gsgp_status gsgp_init(gsgp_ctx *c) {
     TRY(dalloc_n(c, &c->R_genes, (size_t)r * Kr));
     TRY(dalloc_n(c, &c->R_consts, (size_t)r * Kr));
     TRY(dalloc_n(c, &c->R_len, (size_t)r));
+    if (linear) {
+      TRY(dalloc_n(c, &c->Pc_genes, (size_t)m * Kp));
+      TRY(dalloc_n(c, &c->Pc_consts, (size_t)m * Kp));
+      TRY(dalloc_n(c, &c->Pc_len, (size_t)m));
+      TRY(dalloc_n(c, &c->Rc_genes, (size_t)r * Kr));
+      TRY(dalloc_n(c, &c->Rc_consts, (size_t)r * Kr));
+      TRY(dalloc_n(c, &c->Rc_len, (size_t)r));
+    }
     TRY(dalloc_n(c, &c->pool, (size_t)2 * m * c->n_pad));
     const size_t sbytes = cf.sigma_dtype == GSGP_SIGMA_BF16 ? 2 : 4;
     TRY(dalloc(c, &c->sigR, sbytes * (size_t)r * c->n_pad));
@@ -426,13 +456,26 @@ extern "C" gsgp_status gsgp_init(gsgp_ctx *c) {
                              c->P_genes, c->P_consts, c->P_len, c->stream));
     LAUNCH(1, launch_genomes(r, Kr, c->l, k2, cf.run, kPurposeRt, cf.const_lo, cf.const_hi,
                              c->R_genes, c->R_consts, c->R_len, c->stream));
-    // the deepest stack of each pool sizes the interpreter's stack
+    // the live code of each genome, then the deepest stack of each pool,
+    // which sizes the interpreter's stack
+    LAUNCH(1, launch_compact(c->P_genes, c->P_consts, c->P_len, m, Kp, c->Pc_genes, c->Pc_consts,
+                             c->Pc_len, c->stream));
+    LAUNCH(1, launch_compact(c->R_genes, c->R_consts, c->R_len, r, Kr, c->Rc_genes, c->Rc_consts,
+                             c->Rc_len, c->stream));
     CK(cudaMemsetAsync(c->d_stack, 0, 2 * sizeof(int), c->stream));
-    LAUNCH(1, launch_max_stack(c->P_genes, c->P_len, m, Kp, c->d_stack, c->stream));
-    LAUNCH(1, launch_max_stack(c->R_genes, c->R_len, r, Kr, c->d_stack + 1, c->stream));
+    LAUNCH(1, launch_max_stack(c->Pc_genes, c->Pc_len, m, Kp, c->d_stack, c->stream));
+    LAUNCH(1, launch_max_stack(c->Rc_genes, c->Rc_len, r, Kr, c->d_stack + 1, c->stream));
     int h[2] = {0, 0};
     CK(cudaMemcpyAsync(h, c->d_stack, sizeof h, cudaMemcpyDeviceToHost, c->stream));
+    std::vector<int> lp((size_t)m), lr((size_t)r);
+    CK(cudaMemcpyAsync(lp.data(), c->Pc_len, sizeof(int) * lp.size(), cudaMemcpyDeviceToHost,
+                       c->stream));
+    CK(cudaMemcpyAsync(lr.data(), c->Rc_len, sizeof(int) * lr.size(), cudaMemcpyDeviceToHost,
+                       c->stream));
     CK(cudaStreamSynchronize(c->stream));
+    c->eval_genes[0] = c->eval_genes[1] = 0;
+    for (int v : lp) c->eval_genes[0] += v;
+    for (int v : lr) c->eval_genes[1] += v;
     if (h[0] > kMaxStack || h[1] > kMaxStack)
       return fail(c, GSGP_E_INVALID,
                   "a generated genome needs a stack of %d entries (limit %d); use a shorter "
@@ -440,6 +483,8 @@ extern "C" gsgp_status gsgp_init(gsgp_ctx *c) {
     slots_p = h[0] > 1 ? h[0] : 1;
     slots_r = h[1] > 1 ? h[1] : 1;
   } else {
+    c->Pc_genes = nullptr;   // the trees are evaluated as generated
+    c->eval_genes[0] = c->eval_genes[1] = -1;   // counted on request (gsgp_get_info)
     LAUNCH(1, launch_treegen(m, cf.pop_min_depth, cf.pop_max_depth, Kp, c->l, k2, cf.run,
                              kPurposePop, cf.p_grow_function, cf.p_feature_given_terminal,
                              cf.const_lo, cf.const_hi, c->P_genes, c->P_consts, c->P_len,
@@ -458,9 +503,9 @@ extern "C" gsgp_status gsgp_init(gsgp_ctx *c) {
   ip.tiles = c->tiles_interp;
   ip.protect_eps = cf.protect_eps;
   // population semantics + squared errors (rows 0..m-1 of the pool)
-  ip.genes = c->P_genes;
-  ip.consts = c->P_consts;
-  ip.lengths = c->P_len;
+  ip.genes = prog_genes(c, true);
+  ip.consts = prog_consts(c, true);
+  ip.lengths = prog_len(c, true);
   ip.K = Kp;
   ip.stack_slots = slots_p;
   ip.out = c->pool;
@@ -472,9 +517,9 @@ extern "C" gsgp_status gsgp_init(gsgp_ctx *c) {
   LAUNCH(1, launch_interpret(0, ip, m, c->stream));
   if (c->timing) CK(cudaEventRecord(c->ev_init[1], c->stream));
   // random-tree semantics wrapped by the logistic function
-  ip.genes = c->R_genes;
-  ip.consts = c->R_consts;
-  ip.lengths = c->R_len;
+  ip.genes = prog_genes(c, false);
+  ip.consts = prog_consts(c, false);
+  ip.lengths = prog_len(c, false);
   ip.K = Kr;
   ip.stack_slots = slots_r;
   ip.out = c->sigR;
@@ -1023,16 +1068,16 @@ static gsgp_status run_predict(gsgp_ctx *c, const float *X_dev_rows, int64_t n, 
   p.X = Xt;
   p.n_pad = n_pad;
   p.n = n;
-  p.anc_genes = c->P_genes + (size_t)c->ancestor * c->Kp;
-  p.anc_consts = c->P_consts + (size_t)c->ancestor * c->Kp;
+  p.anc_genes = prog_genes(c, true) + (size_t)c->ancestor * c->Kp;
+  p.anc_consts = prog_consts(c, true) + (size_t)c->ancestor * c->Kp;
   int anc_len = 0;
-  CK(cudaMemcpyAsync(&anc_len, c->P_len + c->ancestor, sizeof(int), cudaMemcpyDeviceToHost,
+  CK(cudaMemcpyAsync(&anc_len, prog_len(c, true) + c->ancestor, sizeof(int), cudaMemcpyDeviceToHost,
                      c->stream));
   CK(cudaStreamSynchronize(c->stream));
   p.anc_len = anc_len;
-  p.rt_genes = c->R_genes;
-  p.rt_consts = c->R_consts;
-  p.rt_len = c->R_len;
+  p.rt_genes = prog_genes(c, false);
+  p.rt_consts = prog_consts(c, false);
+  p.rt_len = prog_len(c, false);
   p.Kr = c->Kr;
   p.terms = c->d_terms;
   p.coef = c->d_coef;
@@ -1107,6 +1152,20 @@ extern "C" gsgp_status gsgp_get_info(gsgp_ctx *c, gsgp_info *out) {
       c->shape_ready ? (c->path == 1 ? kPersistGenerations : 1) : 0;
   out->kernel_launches = c->launches;
   out->device_bytes = c->dev_bytes;
+  if (c->state == 2 && c->eval_genes[0] < 0) {   // trees: their lengths, counted once
+    TRY(use_device(c));
+    std::vector<int> lp((size_t)c->cfg.pop_size), lr((size_t)c->cfg.n_random_trees);
+    CK(cudaMemcpyAsync(lp.data(), c->P_len, sizeof(int) * lp.size(), cudaMemcpyDeviceToHost,
+                       c->stream));
+    CK(cudaMemcpyAsync(lr.data(), c->R_len, sizeof(int) * lr.size(), cudaMemcpyDeviceToHost,
+                       c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    c->eval_genes[0] = c->eval_genes[1] = 0;
+    for (int v : lp) c->eval_genes[0] += v;
+    for (int v : lr) c->eval_genes[1] += v;
+  }
+  out->pop_evaluated_genes = c->state == 2 ? c->eval_genes[0] : 0;
+  out->rt_evaluated_genes = c->state == 2 ? c->eval_genes[1] : 0;
   return GSGP_OK;
   API_END(c)
 }

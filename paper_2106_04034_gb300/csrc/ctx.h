@@ -47,6 +47,10 @@ struct gsgp_ctx {
   int64_t layout_key[7] = {0, 0, 0, 0, 0, 0, 0};
   int *P_genes = nullptr, *P_len = nullptr, *R_genes = nullptr, *R_len = nullptr;
   float *P_consts = nullptr, *R_consts = nullptr;
+  // the programs the interpreter and the model evaluate: the live code of
+  // linear genomes (own buffers), or the programs themselves (aliases)
+  int *Pc_genes = nullptr, *Pc_len = nullptr, *Rc_genes = nullptr, *Rc_len = nullptr;
+  float *Pc_consts = nullptr, *Rc_consts = nullptr;
   float *pool = nullptr;
   void *sigR = nullptr;
   int *perm = nullptr;
@@ -66,6 +70,7 @@ struct gsgp_ctx {
   int lin_start_cap = 0;
   int *d_anc = nullptr;
   int *d_stack = nullptr;     // [2] deepest interpreter stack of P and R (linear genomes)
+  int64_t eval_genes[2] = {0, 0};   // genes evaluated per case over P and R
   unsigned *d_flag = nullptr;
   int gen = 0;
 

@@ -143,6 +143,87 @@ cudaError_t launch_genomes(int count, int K, int n_features, uint2 key, uint32_t
   return cudaGetLastError();
 }
 
+// Live code of a linear genome.  The value of a genome is Out, the output
+// of the last function applied (or the stack top if none is applied); every
+// other gene either is a function skipped for lack of operands or produces a
+// value that never reaches Out.  Only the genes of the expression tree under
+// that root matter, and in their original order they form a well-formed
+// postfix program: a function's first operand is complete before its second
+// is started (the stack is last-in first-out).  Evaluating that program
+// applies the same operations to the same operands in the same order, so the
+// result is bit-identical while skipped functions and dead values cost
+// nothing.  One thread per genome: a forward pass marks the applied
+// functions and finds the root, a backward pass from the root counts the
+// values still needed (a terminal supplies one, an applied function supplies
+// one and needs two) and marks the live genes, a last pass copies them.
+// ---------------------------------------------------------------------------
+constexpr int kMaskWords = (kMaxGenomeGenes + 31) / 32;
+
+__global__ void __launch_bounds__(128)
+    compact_kernel(const int *__restrict__ genes, const float *__restrict__ consts,
+                   const int *__restrict__ lengths, int count, int K, int *__restrict__ out_genes,
+                   float *__restrict__ out_consts, int *__restrict__ out_len) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= count) return;
+  const int *g = genes + (size_t)i * K;
+  const float *c = consts + (size_t)i * K;
+  const int len = lengths[i];
+  uint32_t applied[kMaskWords], live[kMaskWords];
+  const int words = (len + 31) / 32;
+  for (int w = 0; w < words; ++w) applied[w] = live[w] = 0u;
+  int sp = 0, root = -1, last_terminal = -1;
+  for (int k = 0; k < len; ++k) {
+    const int op = g[k] & 0xFF;
+    if (op >= kOpConst) {
+      ++sp;
+      last_terminal = k;
+    } else if (sp >= 2) {
+      --sp;
+      applied[k >> 5] |= 1u << (k & 31);
+      root = k;
+    }
+  }
+  if (root < 0) root = last_terminal;   // no function applied: the stack top (or nothing)
+  int need = root >= 0 ? 1 : 0;
+  for (int k = root; k >= 0 && need > 0; --k) {
+    const bool terminal = (g[k] & 0xFF) >= kOpConst;
+    const bool app = (applied[k >> 5] >> (k & 31)) & 1u;
+    if (terminal) {
+      --need;
+    } else if (app) {
+      ++need;
+    } else {
+      continue;
+    }
+    live[k >> 5] |= 1u << (k & 31);
+  }
+  int *og = out_genes + (size_t)i * K;
+  float *oc = out_consts + (size_t)i * K;
+  int n = 0;
+  for (int k = 0; k <= root; ++k) {
+    if ((live[k >> 5] >> (k & 31)) & 1u) {
+      og[n] = g[k];
+      oc[n] = c[k];
+      ++n;
+    }
+  }
+  out_len[i] = n;
+  for (int k = n; k < K; ++k) {
+    og[k] = kGenePad;
+    oc[k] = 0.0f;
+  }
+}
+
+cudaError_t launch_compact(const int *genes, const float *consts, const int *lengths, int count,
+                           int K, int *out_genes, float *out_consts, int *out_len,
+                           cudaStream_t s) {
+  if (count <= 0) return cudaSuccess;
+  if (K > kMaxGenomeGenes) return cudaErrorInvalidValue;
+  compact_kernel<<<(count + 127) / 128, 128, 0, s>>>(genes, consts, lengths, count, K, out_genes,
+                                                      out_consts, out_len);
+  return cudaGetLastError();
+}
+
 // Deepest stack any program of a pool reaches under the interpreter's rule
 // (a function short of operands is skipped): sizes the interpreter's shared
 // memory stack.  One thread per program; *out must be zero before.

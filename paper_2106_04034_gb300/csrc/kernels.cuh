@@ -20,6 +20,11 @@ cudaError_t launch_genomes(int count, int K, int n_features, uint2 key, uint32_t
                            float *consts, int *lengths, cudaStream_t s);
 cudaError_t launch_max_stack(const int *genes, const int *lengths, int count, int K, int *out,
                              cudaStream_t s);
+// The live genes of each linear genome (the expression under register Out),
+// in order: a postfix program with the same value, bit for bit.
+cudaError_t launch_compact(const int *genes, const float *consts, const int *lengths, int count,
+                           int K, int *out_genes, float *out_consts, int *out_len,
+                           cudaStream_t s);
 
 cudaError_t launch_transpose(const float *in, int64_t n, int l, float *out, int64_t n_pad,
                              int64_t col0, cudaStream_t s);
