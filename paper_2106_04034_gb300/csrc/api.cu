@@ -451,6 +451,8 @@ extern "C" gsgp_status gsgp_init(gsgp_ctx *c) {
   const uint2 k2 = make_uint2((uint32_t)(cf.seed & 0xffffffffu), (uint32_t)(cf.seed >> 32));
   // interpreter stack entries below the top: a tree of depth d needs d + 1
   int slots_p = cf.pop_max_depth + 1, slots_r = cf.rt_max_depth + 1;
+  int max_len_p = Kp, max_len_r = Kr;   // longest program of each pool
+  if (linear) max_len_p = max_len_r = 1;
   if (linear) {
     LAUNCH(1, launch_genomes(m, Kp, c->l, k2, cf.run, kPurposePop, cf.const_lo, cf.const_hi,
                              c->P_genes, c->P_consts, c->P_len, c->stream));
@@ -474,8 +476,14 @@ extern "C" gsgp_status gsgp_init(gsgp_ctx *c) {
                        c->stream));
     CK(cudaStreamSynchronize(c->stream));
     c->eval_genes[0] = c->eval_genes[1] = 0;
-    for (int v : lp) c->eval_genes[0] += v;
-    for (int v : lr) c->eval_genes[1] += v;
+    for (int v : lp) {
+      c->eval_genes[0] += v;
+      max_len_p = v > max_len_p ? v : max_len_p;
+    }
+    for (int v : lr) {
+      c->eval_genes[1] += v;
+      max_len_r = v > max_len_r ? v : max_len_r;
+    }
     if (h[0] > kMaxStack || h[1] > kMaxStack)
       return fail(c, GSGP_E_INVALID,
                   "a generated genome needs a stack of %d entries (limit %d); use a shorter "
@@ -507,6 +515,7 @@ extern "C" gsgp_status gsgp_init(gsgp_ctx *c) {
   ip.consts = prog_consts(c, true);
   ip.lengths = prog_len(c, true);
   ip.K = Kp;
+  ip.max_len = max_len_p;
   ip.stack_slots = slots_p;
   ip.out = c->pool;
   ip.partial = c->partial;
@@ -521,6 +530,7 @@ extern "C" gsgp_status gsgp_init(gsgp_ctx *c) {
   ip.consts = prog_consts(c, false);
   ip.lengths = prog_len(c, false);
   ip.K = Kr;
+  ip.max_len = max_len_r;
   ip.stack_slots = slots_r;
   ip.out = c->sigR;
   ip.partial = nullptr;

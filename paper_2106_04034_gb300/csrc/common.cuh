@@ -118,7 +118,8 @@ struct InterpParams {
   const int *genes;          // [count][K]
   const float *consts;       // [count][K]
   const int *lengths;        // [count]
-  int K;
+  int K;                     // row stride of genes / consts
+  int max_len;               // longest program of the pool (sizes shared memory)
   void *out;                 // [count][n_pad] float (population) or sigma (random)
   double2 *partial;          // [count][tiles] (population only)
   int64_t n_pad;

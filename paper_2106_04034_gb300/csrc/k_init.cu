@@ -335,7 +335,7 @@ __global__ void __launch_bounds__(kInterpThreads) interpret_kernel(InterpParams 
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float4 *s_stack = reinterpret_cast<float4 *>(smem_raw);
   int *s_gene = reinterpret_cast<int *>(s_stack + (size_t)p.stack_slots * kInterpThreads);
-  float *s_const = reinterpret_cast<float *>(s_gene + p.K);
+  float *s_const = reinterpret_cast<float *>(s_gene + p.max_len);
   __shared__ float2 s_sub[kInterpThreads / 32];   // sub-block (warp) totals
 
   const int prog = blockIdx.x;
@@ -352,8 +352,6 @@ __global__ void __launch_bounds__(kInterpThreads) interpret_kernel(InterpParams 
   const bool valid = j4 * 4 < p.n_pad;
   const int64_t jj = valid ? j4 : 0;
   float4 tos = make_float4(0.f, 0.f, 0.f, 0.f);
-  float4 out = tos;        // register Out: the last function output
-  bool applied = false;    // uniform across the CTA (depends on the genes only)
   int sp = 0;
   for (int k = 0; k < len; ++k) {
     const int g = s_gene[k];
@@ -376,14 +374,12 @@ __global__ void __launch_bounds__(kInterpThreads) interpret_kernel(InterpParams 
       tos.z = apply_op(op, a.z, tos.z, p.protect_eps);
       tos.w = apply_op(op, a.w, tos.w, p.protect_eps);
       --sp;
-      out = tos;
-      applied = true;
     }
   }
-  // the program's value is Out (Sec. 2.2, "Interpreter"); a program that
-  // applies no function gives its stack top (0 when empty).  For a
-  // well-formed postfix program Out is the final stack top.
-  if (applied) tos = out;
+  // The program's value is register Out (Sec. 2.2, "Interpreter"): every
+  // program interpreted here is well-formed postfix (a ramped half-and-half
+  // tree, or the live code of a linear genome, which ends with the last
+  // function applied), so Out is the final stack top; an empty program is 0.
 
   if (MODE == 0) {
     float str = 0.f, ste = 0.f;
@@ -426,7 +422,7 @@ __global__ void __launch_bounds__(kInterpThreads) interpret_kernel(InterpParams 
 cudaError_t launch_interpret(int mode, const InterpParams &p, int count, cudaStream_t s) {
   if (count <= 0) return cudaSuccess;
   const size_t smem = (size_t)p.stack_slots * kInterpThreads * sizeof(float4) +
-                      (size_t)p.K * (sizeof(int) + sizeof(float));
+                      (size_t)p.max_len * (sizeof(int) + sizeof(float));
   dim3 grid((unsigned)count, (unsigned)((p.n_pad + kInterpTile - 1) / kInterpTile));
   cudaError_t e = cudaSuccess;
   switch (mode) {
