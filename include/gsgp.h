@@ -206,6 +206,9 @@ typedef struct {
   float *rt_consts;         /* in/out, nullable: r * rt_max_genes */
   int32_t *rt_lengths;      /* in/out, nullable: r */
   int32_t sigma_dtype;      /* out */
+  int32_t n_features;       /* out: features of a case */
+  float protect_eps;        /* out: protected division threshold */
+  int32_t init_mode;        /* out: GSGP_INIT_RHH or GSGP_INIT_LINEAR */
 } gsgp_trace;
 
 /* Errors: GSGP_E_STATE (before init), GSGP_E_INVALID, GSGP_E_CUDA. */
@@ -219,6 +222,21 @@ gsgp_status gsgp_predict(gsgp_ctx *ctx, const float *X, int64_t n, double *y_out
 
 /* As gsgp_predict with DEVICE pointers; does not synchronise. */
 gsgp_status gsgp_predict_device(gsgp_ctx *ctx, const float *X, int64_t n, double *y_out);
+
+/* Evaluate a model given as a filled gsgp_trace (as returned by
+ * gsgp_best_trace, possibly saved and loaded again) on n new cases, with no
+ * context: y = ancestor(x) + sum_k coef[k] * q(sigma(R_k(x))) in float64,
+ * q as in gsgp_trace.  Uses ancestor_genes/consts/length, coef, rt_genes,
+ * rt_consts, rt_lengths, max_genes, rt_max_genes, n_random_trees,
+ * sigma_dtype, n_features and protect_eps of *model.  X is row-major
+ * (n x n_features) float32 HOST, y_out n doubles HOST; device work runs on
+ * `stream` (cudaStream_t, NULL = legacy default) of the current device and
+ * the call synchronises it.  err_msg (nullable, err_cap bytes) receives a
+ * message on failure.  Errors: GSGP_E_INVALID (NULL or inconsistent fields,
+ * non-finite X, a program needing more than 32 stack entries), GSGP_E_OOM,
+ * GSGP_E_CUDA. */
+gsgp_status gsgp_model_predict(const gsgp_trace *model, const float *X, int64_t n, double *y_out,
+                               void *stream, char *err_msg, size_t err_cap);
 
 /* Last error message of ctx ("" if none); valid until the next call. */
 const char *gsgp_last_error(const gsgp_ctx *ctx);

@@ -63,7 +63,8 @@ class Trace(C.Structure):
         ("n_random_trees", C.c_int32), ("coef", C.POINTER(C.c_double)),
         ("rt_max_genes", C.c_int32), ("rt_genes", C.POINTER(C.c_int32)),
         ("rt_consts", C.POINTER(C.c_float)), ("rt_lengths", C.POINTER(C.c_int32)),
-        ("sigma_dtype", C.c_int32),
+        ("sigma_dtype", C.c_int32), ("n_features", C.c_int32), ("protect_eps", C.c_float),
+        ("init_mode", C.c_int32),
     ]
 
 
@@ -117,6 +118,8 @@ _SIGS = {
     "gsgp_rng_words": (C.c_int, [C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint32, C.c_int32, P, P]),
     "gsgp_mutate_noalloc": (C.c_int, [P, P, C.c_int64, P, C.c_int64, C.c_int64, P, P, P, P,
                                       C.c_int32, P, P, P, P, C.c_char_p, C.c_size_t]),
+    "gsgp_model_predict": (C.c_int, [C.POINTER(Trace), P, C.c_int64, P, P, C.c_char_p,
+                                     C.c_size_t]),
     "gsgp_batch_create": (C.c_int, [P, C.c_int32, C.POINTER(P)]),
     "gsgp_batch_evolve": (C.c_int, [P, C.c_int32, P, P]),
     "gsgp_batch_set_shape": (C.c_int, [P, C.c_int32, C.c_int32]),
@@ -302,7 +305,8 @@ class Run:
         out.update(best_slot=t.best_slot, best_train_rmse=t.best_train_rmse,
                    best_test_rmse=t.best_test_rmse, ancestor=t.ancestor,
                    ancestor_length=t.ancestor_length, n_generations=G,
-                   sigma_dtype=t.sigma_dtype)
+                   sigma_dtype=t.sigma_dtype, n_features=t.n_features,
+                   protect_eps=t.protect_eps, init_mode=t.init_mode)
         return out
 
     def predict(self, X) -> np.ndarray:
@@ -438,6 +442,39 @@ class Batch:
         i.struct_size = C.sizeof(BatchInfo)
         self._check(self.lib.gsgp_batch_get_info(self.handle, C.byref(i)))
         return i
+
+
+def model_predict(model: dict, X, stream=None) -> np.ndarray:
+    """gsgp_model_predict: evaluate a model (the dict Run.best_trace returns)
+    on HOST cases X (n x n_features), with no run context."""
+    lib = load_library()
+    X = np.ascontiguousarray(X, dtype=np.float32)
+    n = X.shape[0]
+    keep = {k: np.ascontiguousarray(model[k]) for k in
+            ("anc_genes", "anc_consts", "coef", "rt_genes", "rt_consts", "rt_lengths")}
+    t = Trace()
+    t.struct_size = C.sizeof(Trace)
+    t.ancestor_length = int(model["ancestor_length"])
+    t.max_genes = int(keep["anc_genes"].shape[0])
+    t.ancestor_genes = keep["anc_genes"].ctypes.data_as(C.POINTER(C.c_int32))
+    t.ancestor_consts = keep["anc_consts"].ctypes.data_as(C.POINTER(C.c_float))
+    t.n_random_trees = int(keep["coef"].shape[0])
+    t.coef = keep["coef"].ctypes.data_as(C.POINTER(C.c_double))
+    t.rt_max_genes = int(keep["rt_genes"].shape[1])
+    t.rt_genes = keep["rt_genes"].ctypes.data_as(C.POINTER(C.c_int32))
+    t.rt_consts = keep["rt_consts"].ctypes.data_as(C.POINTER(C.c_float))
+    t.rt_lengths = keep["rt_lengths"].ctypes.data_as(C.POINTER(C.c_int32))
+    t.sigma_dtype = int(model["sigma_dtype"])
+    t.n_features = int(model["n_features"])
+    t.protect_eps = float(model["protect_eps"])
+    t.init_mode = int(model["init_mode"])
+    y = np.zeros(n, np.float64)
+    msg = C.create_string_buffer(256)
+    s = None if stream is None else (stream if isinstance(stream, int) else stream.cuda_stream)
+    st = lib.gsgp_model_predict(C.byref(t), _ptr(X), n, _ptr(y), s, msg, 256)
+    if st != OK:
+        raise GsgpError(st, msg.value.decode())
+    return y
 
 
 def rng_words(seed: int, run: int, gen_or_purpose: int, individual: int, n_words: int,

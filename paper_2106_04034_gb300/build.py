@@ -2,8 +2,9 @@
 
 Compiles every ``csrc/*.cu`` translation unit in parallel with nvcc
 (``-gencode arch=compute_103a,code=sm_103a``) and links them into
-``_lib/libgsgp.so`` next to this file.  A stamp of the sources, flags and
-host machine skips the work when nothing changed.
+``_lib/libgsgp.so`` next to this file, then the command-line front end
+``_lib/gsgp`` (``cli/gsgp_cli.cpp``, host C++ over the C ABI).  A stamp of
+the sources, flags and host machine skips the work when nothing changed.
 """
 from __future__ import annotations
 
@@ -21,6 +22,8 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(PKG, "_lib")
 LIB = os.path.join(OUT_DIR, "libgsgp.so")
+CLI_SRC = os.path.join(PKG, "cli", "gsgp_cli.cpp")
+CLI = os.path.join(OUT_DIR, "gsgp")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2", "-prec-div=true", "-prec-sqrt=true", "-ftz=false"]
 
@@ -41,6 +44,7 @@ def _stamp() -> str:
     files = _sources() + sorted(
         os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".h")))
     files.append(os.path.join(INCLUDE, "gsgp.h"))
+    files.append(CLI_SRC)
     for f in files:
         with open(f, "rb") as fh:
             h.update(f.encode() + b"\0" + fh.read())
@@ -53,7 +57,7 @@ def build_library(verbose: bool = False, force: bool = False, ptxas_verbose: boo
     os.makedirs(OUT_DIR, exist_ok=True)
     stamp_file = os.path.join(OUT_DIR, "libgsgp.stamp")
     stamp = _stamp()
-    if (not force and os.path.exists(LIB) and os.path.exists(stamp_file)
+    if (not force and os.path.exists(LIB) and os.path.exists(CLI) and os.path.exists(stamp_file)
             and open(stamp_file).read() == stamp):
         return LIB
     cc = nvcc()
@@ -82,6 +86,14 @@ def build_library(verbose: bool = False, force: bool = False, ptxas_verbose: boo
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
     os.replace(tmp, LIB)
+    # the command-line front end, linked against the library next to it
+    cxx = shutil.which("g++") or "g++"
+    cmd = [cxx, "-O2", "-std=c++17", "-I", INCLUDE, CLI_SRC, "-o", CLI + ".tmp", "-L", OUT_DIR,
+           "-lgsgp", "-Wl,-rpath,$ORIGIN"]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"building the command-line tool failed:\n{r.stdout}\n{r.stderr}")
+    os.replace(CLI + ".tmp", CLI)
     with open(stamp_file, "w") as fh:
         fh.write(stamp)
     return LIB

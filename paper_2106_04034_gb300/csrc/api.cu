@@ -1038,6 +1038,9 @@ extern "C" gsgp_status gsgp_best_trace(gsgp_ctx *c, gsgp_trace *out) {
   out->n_random_trees = c->cfg.n_random_trees;
   out->rt_max_genes = c->Kr;
   out->sigma_dtype = c->cfg.sigma_dtype;
+  out->n_features = c->l;
+  out->protect_eps = c->cfg.protect_eps;
+  out->init_mode = c->cfg.init_mode;
   CK(cudaMemcpyAsync(&out->ancestor_length, c->P_len + c->ancestor, sizeof(int),
                      cudaMemcpyDeviceToHost, c->stream));
   if (out->ancestor_genes)
