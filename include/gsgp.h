@@ -238,6 +238,24 @@ gsgp_status gsgp_predict_device(gsgp_ctx *ctx, const float *X, int64_t n, double
 gsgp_status gsgp_model_predict(const gsgp_trace *model, const float *X, int64_t n, double *y_out,
                                void *stream, char *err_msg, size_t err_cap);
 
+/* Checkpoint of a run after any number of generations: the current
+ * population's semantics and fitness, the generation counter and best slot,
+ * the trace and the best-of-generation log, with the configuration fields
+ * that shape the search and a hash of the targets.  buf (HOST, cap bytes)
+ * receives it; buf = NULL only reports the size in *size_out.
+ * Errors: GSGP_E_STATE (before init), GSGP_E_INVALID (cap too small),
+ * GSGP_E_CUDA, GSGP_E_TIMEOUT. */
+gsgp_status gsgp_checkpoint(gsgp_ctx *ctx, void *buf, size_t cap, size_t *size_out);
+
+/* Resume a checkpointed run in ctx, which holds the same configuration and
+ * the same loaded data: re-runs the initialisation (programs and random-tree
+ * semantics are functions of the configuration and data) and installs the
+ * saved state, so that further gsgp_evolve calls continue bit for bit as the
+ * original run would have.  Errors: GSGP_E_STATE (no data loaded),
+ * GSGP_E_INVALID (not a checkpoint, another configuration or other data,
+ * corrupt sizes), GSGP_E_OOM, GSGP_E_CUDA. */
+gsgp_status gsgp_restore(gsgp_ctx *ctx, const void *buf, size_t size);
+
 /* Last error message of ctx ("" if none); valid until the next call. */
 const char *gsgp_last_error(const gsgp_ctx *ctx);
 

@@ -118,6 +118,8 @@ _SIGS = {
     "gsgp_rng_words": (C.c_int, [C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint32, C.c_int32, P, P]),
     "gsgp_mutate_noalloc": (C.c_int, [P, P, C.c_int64, P, C.c_int64, C.c_int64, P, P, P, P,
                                       C.c_int32, P, P, P, P, C.c_char_p, C.c_size_t]),
+    "gsgp_checkpoint": (C.c_int, [P, P, C.c_size_t, C.POINTER(C.c_size_t)]),
+    "gsgp_restore": (C.c_int, [P, P, C.c_size_t]),
     "gsgp_model_predict": (C.c_int, [C.POINTER(Trace), P, C.c_int64, P, P, C.c_char_p,
                                      C.c_size_t]),
     "gsgp_batch_create": (C.c_int, [P, C.c_int32, C.POINTER(P)]),
@@ -359,6 +361,19 @@ class Run:
         self._check(self.lib.gsgp_get_trace(self.ctx, g0, count, _ptr(a[0]), _ptr(a[1]),
                                             _ptr(a[2]), _ptr(ms)))
         return a[0], a[1], a[2], ms
+
+    def checkpoint(self) -> bytes:
+        """gsgp_checkpoint: the run's state as bytes."""
+        n = C.c_size_t(0)
+        self._check(self.lib.gsgp_checkpoint(self.ctx, None, 0, C.byref(n)))
+        buf = C.create_string_buffer(n.value)
+        self._check(self.lib.gsgp_checkpoint(self.ctx, buf, n.value, C.byref(n)))
+        return buf.raw[:n.value]
+
+    def restore(self, data: bytes):
+        """gsgp_restore: resume from checkpoint bytes (same config and data loaded)."""
+        buf = C.create_string_buffer(data, len(data))
+        self._check(self.lib.gsgp_restore(self.ctx, buf, len(data)))
 
     def set_evolve_shape(self, path: int, vec: int = 0, opb: int = 0):
         self._check(self.lib.gsgp_set_evolve_shape(self.ctx, path, vec, opb))

@@ -766,7 +766,7 @@ static gsgp_status choose_shape(gsgp_ctx *c) {
 }
 
 // Sticky device error of the persistent kernel's barrier (after a sync).
-static gsgp_status check_device_error(gsgp_ctx *c) {
+gsgp_status check_device_error(gsgp_ctx *c) {
   if (!c->gs) return GSGP_OK;
   int err = 0;
   CK(cudaMemcpyAsync(&err, &c->gs->err, sizeof err, cudaMemcpyDeviceToHost, c->stream));

@@ -153,3 +153,6 @@ gsgp_status ensure_trace(gsgp_ctx *c, int need);
 // the backup buffers (on the run's stream) ahead of the first snapshot.
 gsgp_status ensure_backup(gsgp_ctx *c);
 gsgp_status snapshot(gsgp_ctx *c, bool save, cudaStream_t s);
+// GSGP_E_TIMEOUT when a bounded wait of the generation kernel gave up
+// (synchronises the run's stream).
+gsgp_status check_device_error(gsgp_ctx *c);

@@ -180,3 +180,13 @@ def test_linear_genome_config_checks(lib):
     r = pkg.Run(cfg)
     assert r.info().pop_max_genes == 2047 and r.info().rt_max_genes == 2047
     r.close()
+
+
+def test_checkpoint_needs_a_run(lib):
+    r = pkg.Run(pop_size=8, n_random_trees=4)
+    n = C.c_size_t(0)
+    assert lib.gsgp_checkpoint(r.ctx, None, 0, C.byref(n)) == B.E_STATE
+    buf = C.create_string_buffer(64)
+    assert lib.gsgp_restore(r.ctx, buf, 64) == B.E_STATE
+    assert lib.gsgp_restore(None, buf, 64) == B.E_INVALID
+    r.close()
