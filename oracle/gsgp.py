@@ -68,6 +68,7 @@ class Params:
     gsm_sign_plus: bool = False  # the printed "+" form; experiments only
     init_mode: int = 0           # 0 ramped half-and-half trees, 1 the paper's linear genomes
     max_genes: int = 127         # genome length k (init_mode 1)
+    p_crossover: float = 0.0     # probability an offspring comes from crossover (paper: 0)
 
 
 def feature_major(X_rows: np.ndarray) -> np.ndarray:
@@ -109,6 +110,27 @@ def selection_draws(p: Params, g: int):
     else:
         ms = np.full(m, ms32, dtype=np.float32)
     return cand, a, b, ms
+
+
+def crossover_draws(p: Params, g: int):
+    """Crossover draws of generation g (only when p_crossover > 0): words
+    t+3 (crossover iff u24 < p_crossover) and t+4 .. 2t+3 (the second
+    parent's tournament candidates) of each slot's stream.  The mask tree is
+    rt1 (word t).  Returns is_crossover (m,) bool, candidates (m, t)."""
+    m, t = p.pop_size, p.tournament_size
+    W = streams_words(p.seed, p.run, g, m, 2 * t + 4)
+    is_cross = u24(W[:, t + 3]) < float(np.float32(p.p_crossover))
+    cand2 = idx(W[:, t + 4:2 * t + 4], m) if t > 0 else np.zeros((m, 0), dtype=np.int64)
+    return is_cross, cand2
+
+
+def gsc(S_T: np.ndarray, S_R: np.ndarray, p1, p2, c) -> np.ndarray:
+    """Geometric semantic crossover on semantic vectors: with the random
+    function R = sigma(random tree c) in [0, 1], the offspring is
+    R * T1 + (1 - R) * T2 case by case (the original GSGP crossover the
+    paper names beside mutation, Sec. 2)."""
+    Rm = S_R[c]
+    return Rm * S_T[p1] + (1.0 - Rm) * S_T[p2]
 
 
 def tournament(F: np.ndarray, cand: np.ndarray) -> np.ndarray:
@@ -214,6 +236,11 @@ class GSGP:
         g = self.gen
         cand, a, b, ms = selection_draws(p, g)
         parent = tournament(self.F_T, cand)
+        cross = np.zeros(p.pop_size, dtype=bool)
+        parent2 = np.arange(p.pop_size, dtype=np.int64)
+        if p.p_crossover > 0:
+            cross, cand2 = crossover_draws(p, g)
+            parent2 = tournament(self.F_T, cand2)
         elite_slot = None
         if replay is not None:
             rp = np.asarray(replay["parent"], dtype=np.int64)
@@ -223,18 +250,31 @@ class GSGP:
                 raise AssertionError(f"gen {g}: more than one elite entry")
             if len(elite_rows) == 1:
                 elite_slot = int(elite_rows[0])
+            r2 = np.asarray(replay["rt2"], dtype=np.int64)
             for i in range(p.pop_size):
                 if i == elite_slot:
                     continue
-                _check_draws(g, i, replay, a, b, ms, checks)
+                if cross[i]:
+                    # crossover entry: (parent 1, mask tree, -2 - parent 2, 0)
+                    if int(r1[i]) != int(a[i]) or int(r2[i]) > -2:
+                        _note(checks, "draw_mismatch", (g, i))
+                    gp2 = -2 - int(r2[i])
+                    _check_winner(g, i, gp2, cand2[i], self.F_T, checks)
+                    parent2[i] = gp2
+                else:
+                    _check_draws(g, i, replay, a, b, ms, checks)
                 _check_winner(g, i, int(rp[i]), cand[i], self.F_T, checks)
                 parent[i] = rp[i]
         S_O = gsm(self.S_T, self.S_R, parent, a, b, ms, p.gsm_sign_plus)
+        if cross.any():
+            S_O[cross] = gsc(self.S_T, self.S_R, parent[cross], parent2[cross], a[cross])
         F_O, F_O_te = rmse(S_O, self.t, self.n_train)
         t_parent = parent.astype(np.int32).copy()
         t_rt1 = a.astype(np.int32).copy()
         t_rt2 = b.astype(np.int32).copy()
         t_ms = ms.copy()
+        t_rt2[cross] = (-2 - parent2[cross]).astype(np.int32)
+        t_ms[cross] = np.float32(0)
         dec = elitism_decision(self.F_T, F_O) if p.elitism else None
         if replay is not None:
             gpu_dec = None
@@ -278,9 +318,14 @@ class GSGP:
         return reconstruct(self.trace(), slot, self.p.n_random_trees)
 
     def predict(self, X_rows, slot: Optional[int] = None) -> np.ndarray:
+        if slot is None:
+            slot = self.best_slot()
+        if self.p.p_crossover > 0:
+            return predict_replay(self.trace(), slot, self.P, self.R, feature_major(X_rows),
+                                  self.p.protect_eps, self.p.sigma_bf16, self.p.init_mode == 1)
         anc, c = self.reconstruct(slot)
         return predict(self.P, self.R, anc, c, feature_major(X_rows),
-                       self.p.protect_eps, self.p.sigma_bf16)
+                       self.p.protect_eps, self.p.sigma_bf16, self.p.init_mode == 1)
 
 
 def reconstruct(trace, slot: int, n_random_trees: int):
@@ -317,6 +362,35 @@ def predict(P, R, ancestor: int, coef, X_fm, protect_eps=1e-3, sigma_bf16=False,
             s = bf16_round(s)
         y = y + coef[k] * s
     return y
+
+
+def predict_replay(trace, slot: int, P, R, X_fm, protect_eps=1e-3, sigma_bf16=False,
+                   linear=False):
+    """Value of individual `slot` after the traced generations on new cases
+    X_fm (l, n), by replaying the trace on them: the initial population and
+    the random trees are evaluated on the new cases, then every generation
+    applies its recorded mutation (parent + ms (sigma_a - sigma_b)),
+    crossover (rt2 = -2 - parent 2: R parent1 + (1 - R) parent2, R =
+    sigma(rt1)) or elite copy (rt1 = -1).  Holds for any run, with or
+    without crossover."""
+    S = pool_semantics(*P, X_fm, protect_eps, linear=linear)
+    Sr = pool_semantics(*R, X_fm, protect_eps, logistic=True, bf16=sigma_bf16, linear=linear)
+    parent, rt1, rt2, ms = trace
+    for g in range(len(parent)):
+        pa = np.asarray(parent[g], dtype=np.int64)
+        a = np.asarray(rt1[g], dtype=np.int64)
+        b = np.asarray(rt2[g], dtype=np.int64)
+        step = np.asarray(ms[g], dtype=np.float64)[:, None]
+        new = np.empty_like(S)
+        copy = a < 0
+        cross = ~copy & (b <= -2)
+        mut = ~copy & ~cross
+        new[copy] = S[pa[copy]]
+        new[mut] = S[pa[mut]] + step[mut] * (Sr[a[mut]] - Sr[b[mut]])
+        if cross.any():
+            new[cross] = gsc(S, Sr, pa[cross], -2 - b[cross], a[cross])
+        S = new
+    return S[slot]
 
 
 # ---- replay checks (a second implementation's trace against this one) ----
