@@ -86,6 +86,16 @@ enum { GSGP_SIGMA_F32 = 0, GSGP_SIGMA_BF16 = 1 };
  *     genome whose stack would exceed 32 entries is rejected by gsgp_init
  *     (GSGP_E_INVALID). */
 enum { GSGP_INIT_RHH = 0, GSGP_INIT_LINEAR = 1 };
+
+/* Geometric semantic crossover (the GSGP crossover the paper names beside
+ * mutation, Sec. 2; its experiments use probability 0, the default): with
+ * probability p_crossover an offspring is R * T1 + (1 - R) * T2 case by case,
+ * R = sigma of a random tree, T1 and T2 two tournament winners, computed as
+ * T2 + R (T1 - T2) in float32.  Its trace entry is (parent 1, mask tree,
+ * -2 - parent 2, 0).  Runs with crossover have no ancestor-plus-coefficients
+ * model (gsgp_best_trace returns GSGP_E_STATE); gsgp_predict then replays
+ * the trace on the new cases in float64.  The TMA-staged stream shapes do
+ * not support crossover. */
 enum { GSGP_POOL_POPULATION = 0, GSGP_POOL_RANDOM = 1 };
 
 /* Optional device allocator.  alloc returns device memory of at least
@@ -113,6 +123,7 @@ typedef struct {
   int32_t sigma_dtype;         /* GSGP_SIGMA_F32 or GSGP_SIGMA_BF16 storage of sigma(R) */
   int32_t init_mode;           /* GSGP_INIT_RHH or GSGP_INIT_LINEAR (see below) */
   int32_t max_genes;           /* GSGP_INIT_LINEAR: genome length k, 1 .. 4095 */
+  float p_crossover;           /* probability of geometric semantic crossover (see below) */
   void *stream;                /* cudaStream_t for all device work */
   gsgp_alloc_fn alloc;         /* optional device allocator (see above) */
   gsgp_free_fn free;
@@ -122,8 +133,8 @@ typedef struct {
 /* Fill *cfg with defaults: seed 1, run 0, m = 1024, r = 1024, depths 2-6,
  * constants in [-1, 1), p_grow 0.5, p_feature 7/9, protect_eps 1e-3,
  * ms 0.1 fixed, tournament 4, elitism on, float32 sigma, ramped
- * half-and-half programs (max_genes 127 for linear genomes), NULL stream
- * and allocator.  No CUDA call. */
+ * half-and-half programs (max_genes 127 for linear genomes), no crossover,
+ * NULL stream and allocator.  No CUDA call. */
 void gsgp_config_default(gsgp_config *cfg);
 
 /* Reason *cfg would be rejected by gsgp_create, or "" when it is valid.

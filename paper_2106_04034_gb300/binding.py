@@ -45,7 +45,7 @@ class Config(C.Structure):
         ("p_grow_function", C.c_float), ("p_feature_given_terminal", C.c_float),
         ("protect_eps", C.c_float), ("ms", C.c_float), ("ms_mode", C.c_int32),
         ("tournament_size", C.c_int32), ("elitism", C.c_int32), ("sigma_dtype", C.c_int32),
-        ("init_mode", C.c_int32), ("max_genes", C.c_int32),
+        ("init_mode", C.c_int32), ("max_genes", C.c_int32), ("p_crossover", C.c_float),
         ("stream", C.c_void_p), ("alloc", ALLOC_FN), ("free", FREE_FN),
         ("alloc_user", C.c_void_p),
     ]

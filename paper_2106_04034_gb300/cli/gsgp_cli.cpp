@@ -15,8 +15,10 @@
 // fields of gsgp_config (seed, run, pop_size, n_random_trees, pop_min_depth,
 // pop_max_depth, rt_min_depth, rt_max_depth, const_lo, const_hi,
 // p_grow_function, p_feature_given_terminal, protect_eps, ms, ms_mode,
-// tournament_size, elitism, sigma_dtype, init_mode, max_genes) plus
-// generations and runs.  Run k uses Philox counter word run + k.
+// tournament_size, elitism, sigma_dtype, init_mode, max_genes, p_crossover)
+// plus generations and runs.  Run k uses Philox counter word run + k.  Runs
+// with crossover (p_crossover > 0) write no model file: their best
+// individual is not an ancestor plus coefficients.
 #include <algorithm>
 #include <cerrno>
 #include <cmath>
@@ -137,7 +139,7 @@ Settings read_config(const std::string &path) {
         {"const_lo", &f.const_lo}, {"const_hi", &f.const_hi},
         {"p_grow_function", &f.p_grow_function},
         {"p_feature_given_terminal", &f.p_feature_given_terminal},
-        {"protect_eps", &f.protect_eps}, {"ms", &f.ms}};
+        {"protect_eps", &f.protect_eps}, {"ms", &f.ms}, {"p_crossover", &f.p_crossover}};
     if (ints.count(key)) {
       *ints.at(key) = (int32_t)v;
     } else if (floats.count(key)) {
@@ -313,6 +315,13 @@ int run_mode(const std::string &train, const std::string &test, const std::strin
   fclose(b);
   for (int k = 0; k < R; ++k) {
     gsgp_ctx *c = runs[(size_t)k];
+    if (s.cfg.p_crossover > 0.0f) {
+      if (G > 0)
+        printf("run %d: best training RMSE %.9g, test RMSE %.9g\n", k,
+               btr[(size_t)k * G + G - 1], bte[(size_t)k * G + G - 1]);
+      gsgp_destroy(c);
+      continue;
+    }
     gsgp_trace t{};
     t.struct_size = sizeof t;
     check(gsgp_best_trace(c, &t), c, "gsgp_best_trace");   // sizes

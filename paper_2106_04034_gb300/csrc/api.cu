@@ -164,6 +164,7 @@ extern "C" void gsgp_config_default(gsgp_config *cfg) {
   cfg->sigma_dtype = GSGP_SIGMA_F32;
   cfg->init_mode = GSGP_INIT_RHH;
   cfg->max_genes = 127;
+  cfg->p_crossover = 0.0f;
 }
 
 static bool prob_ok(float p) { return std::isfinite(p) && p >= 0.0f && p <= 1.0f; }
@@ -182,7 +183,8 @@ static const char *check_config(const gsgp_config *cfg) {
   if (!std::isfinite(cfg->const_lo) || !std::isfinite(cfg->const_hi) ||
       cfg->const_lo > cfg->const_hi)
     return "constant range must be finite with lo <= hi";
-  if (!prob_ok(cfg->p_grow_function) || !prob_ok(cfg->p_feature_given_terminal))
+  if (!prob_ok(cfg->p_grow_function) || !prob_ok(cfg->p_feature_given_terminal) ||
+      !prob_ok(cfg->p_crossover))
     return "probabilities must be in [0, 1]";
   if (!std::isfinite(cfg->protect_eps) || cfg->protect_eps < 0.0f)
     return "protect_eps must be finite and >= 0";
@@ -370,6 +372,7 @@ GenParams gen_params(gsgp_ctx *c) {
   p.key = make_uint2((uint32_t)(c->cfg.seed & 0xffffffffu), (uint32_t)(c->cfg.seed >> 32));
   p.run = c->cfg.run;
   p.elitism = c->cfg.elitism;
+  p.p_crossover = c->cfg.p_crossover;
   return p;
 }
 
@@ -927,6 +930,8 @@ extern "C" gsgp_status gsgp_set_evolve_shape(gsgp_ctx *c, int32_t path, int32_t 
     if (path == 1 && !persist_shape_supported(sh))
       return fail(c, GSGP_E_INVALID,
                   "persistent shape: vec in {1,2} with opb in {1,2,4}, or vec in {1,2,4} with opb 0");
+    if (path == 1 && opb == 0 && c->cfg.p_crossover > 0.0f)
+      return fail(c, GSGP_E_INVALID, "the TMA-staged stream does not support crossover");
     if (path == 2 && !gen_shape_supported(sh))
       return fail(c, GSGP_E_INVALID, "chained shape must have vec in {1,2,4}, opb in {2,4,8}");
   }
@@ -939,6 +944,9 @@ extern "C" gsgp_status gsgp_set_evolve_shape(gsgp_ctx *c, int32_t path, int32_t 
 }
 
 // ------------------------------------------------------- best individual --
+// Runs with crossover keep no ancestor-plus-coefficients model.
+static bool with_crossover(const gsgp_ctx *c) { return c->cfg.p_crossover > 0.0f; }
+
 static gsgp_status build_model(gsgp_ctx *c) {
   if (c->model_gen == c->gen) return GSGP_OK;
   const int m = c->cfg.pop_size, r = c->cfg.n_random_trees;
@@ -1026,6 +1034,10 @@ extern "C" gsgp_status gsgp_best_trace(gsgp_ctx *c, gsgp_trace *out) {
   if (!out || out->struct_size != sizeof(gsgp_trace))
     return fail(c, GSGP_E_INVALID, "gsgp_trace NULL or struct_size mismatch");
   if (c->state != 2) return fail(c, GSGP_E_STATE, "gsgp_best_trace before gsgp_init");
+  if (with_crossover(c))
+    return fail(c, GSGP_E_STATE,
+                "a run with crossover has no ancestor-plus-coefficients model; gsgp_predict "
+                "replays its trace");
   TRY(use_device(c));
   TRY(build_model(c));
   const int G = c->gen;
@@ -1103,6 +1115,41 @@ static gsgp_status run_predict(gsgp_ctx *c, const float *X_dev_rows, int64_t n, 
   return GSGP_OK;
 }
 
+// Runs with crossover: replay every generation on the new cases (float64).
+static gsgp_status run_predict_replay(gsgp_ctx *c, const float *X_dev_rows, int64_t n,
+                                      double *y_dev) {
+  const int m = c->cfg.pop_size, r = c->cfg.n_random_trees;
+  const int64_t n_pad = (n + 3) / 4 * 4;
+  float *Xt = nullptr;
+  double *S0 = nullptr, *S1 = nullptr, *Sr = nullptr;
+  TRY(dalloc_n(c, &Xt, (size_t)c->l * n_pad));
+  TRY(dalloc_n(c, &S0, (size_t)m * n_pad));
+  TRY(dalloc_n(c, &S1, (size_t)m * n_pad));
+  TRY(dalloc_n(c, &Sr, (size_t)r * n_pad));
+  LAUNCH(1, launch_transpose(X_dev_rows, n, c->l, Xt, n_pad, 0, c->stream));
+  LAUNCH(1, launch_eval_pool(prog_genes(c, true), prog_consts(c, true), prog_len(c, true), c->Kp,
+                             m, Xt, n_pad, n, S0, c->cfg.protect_eps, 0, c->stream));
+  LAUNCH(1, launch_eval_pool(prog_genes(c, false), prog_consts(c, false), prog_len(c, false),
+                             c->Kr, r, Xt, n_pad, n, Sr, c->cfg.protect_eps,
+                             c->cfg.sigma_dtype == GSGP_SIGMA_BF16 ? 2 : 1, c->stream));
+  for (int g = 0; g < c->gen; ++g) {
+    LAUNCH(1, launch_replay(c->trace + (size_t)g * m, m, S0, S1, Sr, n_pad, n, c->stream));
+    double *t = S0;
+    S0 = S1;
+    S1 = t;
+  }
+  DevState st{};
+  CK(cudaMemcpyAsync(&st, c->dstate, sizeof st, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  CK(cudaMemcpyAsync(y_dev, S0 + (size_t)st.best_slot * n_pad, sizeof(double) * (size_t)n,
+                     cudaMemcpyDeviceToDevice, c->stream));
+  dfree(c, Xt);
+  dfree(c, S0);
+  dfree(c, S1);
+  dfree(c, Sr);
+  return GSGP_OK;
+}
+
 extern "C" gsgp_status gsgp_predict(gsgp_ctx *c, const float *X, int64_t n, double *y_out) {
   API_GUARD(c)
   if (c->state != 2) return fail(c, GSGP_E_STATE, "gsgp_predict before gsgp_init");
@@ -1110,13 +1157,16 @@ extern "C" gsgp_status gsgp_predict(gsgp_ctx *c, const float *X, int64_t n, doub
   if (n == 0) return GSGP_OK;
   if (!host_finite(X, n * c->l)) return fail(c, GSGP_E_INVALID, "non-finite value in X");
   TRY(use_device(c));
-  TRY(build_model(c));
+  if (!with_crossover(c)) TRY(build_model(c));
   float *Xd = nullptr;
   double *yd = nullptr;
   TRY(dalloc_n(c, &Xd, (size_t)n * c->l));
   TRY(dalloc_n(c, &yd, (size_t)n));
   CK(cudaMemcpyAsync(Xd, X, sizeof(float) * (size_t)n * c->l, cudaMemcpyHostToDevice, c->stream));
-  TRY(run_predict(c, Xd, n, yd));
+  if (with_crossover(c))
+    TRY(run_predict_replay(c, Xd, n, yd));
+  else
+    TRY(run_predict(c, Xd, n, yd));
   CK(cudaMemcpyAsync(y_out, yd, sizeof(double) * (size_t)n, cudaMemcpyDeviceToHost, c->stream));
   dfree(c, Xd);
   dfree(c, yd);
@@ -1132,6 +1182,10 @@ extern "C" gsgp_status gsgp_predict_device(gsgp_ctx *c, const float *X, int64_t 
   if (n < 0 || (n > 0 && (!X || !y_out))) return fail(c, GSGP_E_INVALID, "bad predict arguments");
   if (n == 0) return GSGP_OK;
   TRY(use_device(c));
+  if (with_crossover(c)) {
+    TRY(run_predict_replay(c, X, n, y_out));
+    return GSGP_OK;
+  }
   TRY(build_model(c));
   TRY(run_predict(c, X, n, y_out));
   return GSGP_OK;

@@ -98,7 +98,8 @@ void free_graph(gsgp_batch *b) {
 
 // GenParams has no padding, so launch arguments built from zeroed storage
 // compare equal byte for byte exactly when their values are equal.
-static_assert(sizeof(GenParams) == 12 * sizeof(void *) + 8 + 8 * 4 + 8 + 8, "GenParams padding");
+static_assert(sizeof(GenParams) == 12 * sizeof(void *) + 8 + 8 * 4 + 8 + 8 + 8,
+              "GenParams padding");
 
 int64_t run_items(const gsgp_ctx *c, const GenShape &sh) {
   const int64_t tiles = (c->n_pad + 1024 * sh.vec - 1) / (1024 * sh.vec);

@@ -27,7 +27,8 @@ struct Header {
   int64_t n_train, n_test;
   int32_t pop_min_depth, pop_max_depth, rt_min_depth, rt_max_depth;
   int32_t init_mode, max_genes, sigma_dtype, tournament_size, elitism, ms_mode;
-  float const_lo, const_hi, p_grow_function, p_feature_given_terminal, protect_eps, ms;
+  float const_lo, const_hi, p_grow_function, p_feature_given_terminal, protect_eps, ms,
+      p_crossover;
   uint64_t target_hash;   // FNV-1a of the targets' bytes
   // state
   int32_t generation, best_slot;
@@ -69,6 +70,7 @@ void fill_identity(const gsgp_ctx *c, Header &h) {
   h.p_feature_given_terminal = f.p_feature_given_terminal;
   h.protect_eps = f.protect_eps;
   h.ms = f.ms;
+  h.p_crossover = f.p_crossover;
 }
 
 bool same_identity(const Header &a, const Header &b) {
@@ -79,7 +81,7 @@ bool same_identity(const Header &a, const Header &b) {
          a.rt_max_depth == b.rt_max_depth && a.init_mode == b.init_mode &&
          a.max_genes == b.max_genes && a.sigma_dtype == b.sigma_dtype &&
          a.tournament_size == b.tournament_size && a.elitism == b.elitism &&
-         a.ms_mode == b.ms_mode && !memcmp(&a.const_lo, &b.const_lo, 6 * sizeof(float)) &&
+         a.ms_mode == b.ms_mode && !memcmp(&a.const_lo, &b.const_lo, 7 * sizeof(float)) &&
          a.target_hash == b.target_hash;
 }
 

@@ -109,6 +109,8 @@ struct GenParams {
   uint2 key;
   uint32_t run;
   int elitism;
+  float p_crossover;         // probability of geometric semantic crossover (0: mutation only)
+  int reserved;
 };
 
 // Parameters of the interpreter (ComputeSemantics) kernel.

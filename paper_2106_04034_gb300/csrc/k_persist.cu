@@ -127,9 +127,9 @@ __device__ __forceinline__ void select_phase(const GenParams &p, const GenState 
           if (!pd.active) return __ldcg(pm + s);
           return (pd.elite && s == pd.w) ? __ldcg(pm + pd.bP) : __ldcg(pm + m + s);
         });
-    p.sel[i] = make_int4(d.prow, orow, d.a, d.b);
+    p.sel[i] = sel_entry(d, orow);
     p.sel_ms[i] = d.ms;
-    p.trace[(size_t)g * m + i] = make_int4(d.parent, d.a, d.b, __float_as_int(d.ms));
+    p.trace[(size_t)g * m + i] = trace_entry(d);
   }
 }
 

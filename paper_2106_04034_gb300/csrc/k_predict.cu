@@ -179,6 +179,73 @@ __global__ void __launch_bounds__(kPredWarps * 32) predict_kernel(const PredictP
   }
 }
 
+// ---------------------------------------------------------------------------
+// Prediction by replaying the trace (runs with crossover, whose model is not
+// an ancestor plus coefficients): every program of a pool evaluated on the
+// new cases in float64 (random trees wrapped by the logistic, or by the
+// training's bf16 rounding), then each generation's recorded operation
+// applied to every slot: copy (rt1 < 0), crossover (rt2 <= -2: R T1 +
+// (1 - R) T2 with R = sigma(rt1)) or mutation (T + ms (sigma_a - sigma_b)).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(128)
+    eval_pool_kernel(const int *__restrict__ genes, const float *__restrict__ consts,
+                     const int *__restrict__ lengths, int K, const float *__restrict__ X,
+                     int64_t n_pad, int64_t n, double *__restrict__ out, float eps, int mode) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int prog = blockIdx.y;
+  if (j >= n) return;
+  const int *g = genes + (size_t)prog * K;
+  const float *c = consts + (size_t)prog * K;
+  double v;
+  if (mode == 2) {   // the training's bf16 sigma
+    const float f = eval_program32(g, c, lengths[prog], X, n_pad, j, eps);
+    v = (double)__bfloat162float(__float2bfloat16_rn(1.0f / (1.0f + expf(-f))));
+  } else {
+    v = eval_program64(g, c, lengths[prog], X, n_pad, j, (double)eps);
+    if (mode == 1) v = 1.0 / (1.0 + exp(-v));
+  }
+  out[(size_t)prog * n_pad + j] = v;
+}
+
+__global__ void __launch_bounds__(128)
+    replay_kernel(const int4 *__restrict__ entries, const double *__restrict__ prev,
+                  double *__restrict__ next, const double *__restrict__ sig, int64_t n_pad,
+                  int64_t n) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = blockIdx.y;
+  if (j >= n) return;
+  const int4 e = entries[i];
+  const double t1 = prev[(size_t)e.x * n_pad + j];
+  double v;
+  if (e.y < 0) {
+    v = t1;
+  } else if (e.z <= -2) {
+    const double rm = sig[(size_t)e.y * n_pad + j];
+    v = rm * t1 + (1.0 - rm) * prev[(size_t)(-2 - e.z) * n_pad + j];
+  } else {
+    const double ms = (double)__int_as_float(e.w);
+    v = t1 + ms * (sig[(size_t)e.y * n_pad + j] - sig[(size_t)e.z * n_pad + j]);
+  }
+  next[(size_t)i * n_pad + j] = v;
+}
+
+cudaError_t launch_eval_pool(const int *genes, const float *consts, const int *lengths, int K,
+                             int count, const float *X, int64_t n_pad, int64_t n, double *out,
+                             float eps, int mode, cudaStream_t s) {
+  if (count <= 0 || n <= 0) return cudaSuccess;
+  eval_pool_kernel<<<dim3((unsigned)((n + 127) / 128), (unsigned)count), 128, 0, s>>>(
+      genes, consts, lengths, K, X, n_pad, n, out, eps, mode);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_replay(const int4 *entries, int m, const double *prev, double *next,
+                          const double *sig, int64_t n_pad, int64_t n, cudaStream_t s) {
+  if (m <= 0 || n <= 0) return cudaSuccess;
+  replay_kernel<<<dim3((unsigned)((n + 127) / 128), (unsigned)m), 128, 0, s>>>(entries, prev, next,
+                                                                            sig, n_pad, n);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_predict(const PredictParams &p, cudaStream_t s) {
   if (p.n <= 0) return cudaSuccess;
   predict_kernel<<<(unsigned)((p.n + 31) / 32), kPredWarps * 32, 0, s>>>(p);

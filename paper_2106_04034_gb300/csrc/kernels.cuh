@@ -127,6 +127,15 @@ struct PredictParams {
 };
 cudaError_t launch_predict(const PredictParams &p, cudaStream_t s);
 
+// Prediction by replaying the trace (k_predict.cu): float64 values of every
+// program of a pool on new cases (mode 0 plain, 1 logistic, 2 the bf16
+// sigma of training), and one generation's recorded operations on every slot.
+cudaError_t launch_eval_pool(const int *genes, const float *consts, const int *lengths, int K,
+                             int count, const float *X, int64_t n_pad, int64_t n, double *out,
+                             float eps, int mode, cudaStream_t s);
+cudaError_t launch_replay(const int4 *entries, int m, const double *prev, double *next,
+                          const double *sig, int64_t n_pad, int64_t n, cudaStream_t s);
+
 cudaError_t launch_rng_words(uint2 key, uint32_t run, uint32_t gp, uint32_t individual,
                              int n_words, uint32_t *out, cudaStream_t s);
 

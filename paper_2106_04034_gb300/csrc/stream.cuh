@@ -42,47 +42,81 @@ struct SigLoad<__nv_bfloat16> {
 struct Draws {
   int parent, a, b, prow;
   float ms;
+  bool cross;          // geometric semantic crossover instead of mutation
+  int parent2, prow2;  // its second parent (slot, row)
 };
+
+// The draws as the stream reads them: (parent row, offspring row, rt1, rt2)
+// for a mutation, (parent row, offspring row, mask tree, -1 - second parent
+// row) for a crossover; and as the trace records them: (parent, rt1, rt2,
+// ms bits) for a mutation, (parent, mask tree, -2 - second parent, 0) for a
+// crossover.
+__device__ __forceinline__ int4 sel_entry(const Draws &d, int orow) {
+  return make_int4(d.prow, orow, d.a, d.cross ? -1 - d.prow2 : d.b);
+}
+__device__ __forceinline__ int4 trace_entry(const Draws &d) {
+  return d.cross ? make_int4(d.parent, d.a, -2 - d.parent2, 0)
+                 : make_int4(d.parent, d.a, d.b, __float_as_int(d.ms));
+}
+
+// Tournament of t candidates drawn from the stream: the smallest training
+// RMSE wins, the earliest drawn on ties; t = 0 keeps slot i.  Candidates'
+// fitness and rows are fetched kBatch at a time, one memory round trip each.
+template <typename FitFn, typename RowFn>
+__device__ __forceinline__ void tournament(const GenParams &p, int i, WordStream &ws, FitFn fit,
+                                           RowFn row, int &winner, int &winner_row) {
+  if (p.tsize == 0) {
+    winner = i;
+    winner_row = row(i);
+    return;
+  }
+  unsigned long long best = 0;
+  constexpr int kBatch = 4;
+  for (int k0 = 0; k0 < p.tsize; k0 += kBatch) {
+    int c[kBatch];
+    unsigned long long f[kBatch];
+    int r[kBatch];
+    const int n = min(kBatch, p.tsize - k0);
+#pragma unroll
+    for (int k = 0; k < kBatch; ++k)
+      if (k < n) c[k] = (int)draw_index(ws.next(), (uint32_t)p.m);
+#pragma unroll
+    for (int k = 0; k < kBatch; ++k)
+      if (k < n) {
+        f[k] = fit_key(fit(c[k]));
+        r[k] = row(c[k]);
+      }
+#pragma unroll
+    for (int k = 0; k < kBatch; ++k)
+      if (k < n && (k0 + k == 0 || f[k] < best)) {   // strict: earliest drawn wins ties
+        best = f[k];
+        winner = c[k];
+        winner_row = r[k];
+      }
+  }
+}
 
 template <typename FitFn, typename RowFn>
 __device__ __forceinline__ Draws draw_offspring(const GenParams &p, int i, int g, FitFn fit,
                                                 RowFn row) {
   WordStream ws(p.key, (uint32_t)i, (uint32_t)g, p.run);
   Draws d;
-  if (p.tsize == 0) {
-    d.parent = i;
-    d.prow = row(i);
-  } else {
-    unsigned long long best = 0;
-    constexpr int kBatch = 4;
-    for (int k0 = 0; k0 < p.tsize; k0 += kBatch) {
-      int c[kBatch];
-      unsigned long long f[kBatch];
-      int r[kBatch];
-      const int n = min(kBatch, p.tsize - k0);
-#pragma unroll
-      for (int k = 0; k < kBatch; ++k)
-        if (k < n) c[k] = (int)draw_index(ws.next(), (uint32_t)p.m);
-#pragma unroll
-      for (int k = 0; k < kBatch; ++k)
-        if (k < n) {
-          f[k] = fit_key(fit(c[k]));
-          r[k] = row(c[k]);
-        }
-#pragma unroll
-      for (int k = 0; k < kBatch; ++k)
-        if (k < n && (k0 + k == 0 || f[k] < best)) {   // strict: earliest drawn wins ties
-          best = f[k];
-          d.parent = c[k];
-          d.prow = r[k];
-        }
-    }
-  }
+  tournament(p, i, ws, fit, row, d.parent, d.prow);
   d.a = (int)draw_index(ws.next(), (uint32_t)p.r);
   d.b = (int)draw_index(ws.next(), (uint32_t)p.r);
   const uint32_t wms = ws.next();
   d.ms = p.ms;
   if (p.ms_mode == 1) d.ms = __double2float_rn(__dmul_rn((double)p.ms, (double)draw_u24(wms)));
+  // geometric semantic crossover (only when enabled, so that mutation-only
+  // runs draw exactly the words above): word t+3 decides, words t+4 .. 2t+3
+  // are the second parent's tournament; the mask is random tree a
+  d.cross = false;
+  d.parent2 = d.parent;
+  d.prow2 = d.prow;
+  if (p.p_crossover > 0.0f) {
+    d.cross = draw_u24(ws.next()) < p.p_crossover;
+    if (d.cross) tournament(p, i, ws, fit, row, d.parent2, d.prow2);
+  }
   return d;
 }
 
@@ -102,6 +136,34 @@ __device__ __forceinline__ void mutate4(const GenParams &p, const float *src, fl
   o.y = fmaf(step, a4.y - b4.y, s.y);
   o.z = fmaf(step, a4.z - b4.z, s.z);
   o.w = fmaf(step, a4.w - b4.w, s.w);
+  *reinterpret_cast<float4 *>(dst + j0) = o;
+  const float dd[4] = {o.x - t4.x, o.y - t4.y, o.z - t4.z, o.w - t4.w};
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    if (j0 + q < p.n_train)
+      str += dd[q] * dd[q];
+    else if (j0 + q < p.n_cases)
+      ste += dd[q] * dd[q];
+  }
+}
+
+// Geometric semantic crossover of 4 consecutive cases: with R = sigma of the
+// mask tree, offspring = R T1 + (1 - R) T2, computed as T2 + R (T1 - T2)
+// (one subtraction and one fused multiply-add per case), and the squared
+// errors as in mutate4.
+template <typename SigT>
+__device__ __forceinline__ void crossover4(const GenParams &p, const float *src1,
+                                           const float *src2, float *dst, const SigT *rm,
+                                           int64_t j0, float &str, float &ste) {
+  const float4 s1 = __ldcg(reinterpret_cast<const float4 *>(src1 + j0));
+  const float4 s2 = __ldcg(reinterpret_cast<const float4 *>(src2 + j0));
+  const float4 r4 = SigLoad<SigT>::load(rm, j0);
+  const float4 t4 = __ldg(reinterpret_cast<const float4 *>(p.target + j0));
+  float4 o;
+  o.x = fmaf(r4.x, s1.x - s2.x, s2.x);
+  o.y = fmaf(r4.y, s1.y - s2.y, s2.y);
+  o.z = fmaf(r4.z, s1.z - s2.z, s2.z);
+  o.w = fmaf(r4.w, s1.w - s2.w, s2.w);
   *reinterpret_cast<float4 *>(dst + j0) = o;
   const float dd[4] = {o.x - t4.x, o.y - t4.y, o.z - t4.z, o.w - t4.w};
 #pragma unroll
@@ -163,9 +225,9 @@ __device__ __forceinline__ void select_offspring(const GenParams &p, int i, int 
   const Draws d = draw_offspring(
       p, i, g, [&](int slot) { return __ldcg(F + slot); },
       [&](int slot) { return __ldcg(perm + slot); });
-  p.sel[i] = make_int4(d.prow, orow, d.a, d.b);
+  p.sel[i] = sel_entry(d, orow);
   p.sel_ms[i] = d.ms;
-  p.trace[(size_t)g * m + i] = make_int4(d.parent, d.a, d.b, __float_as_int(d.ms));
+  p.trace[(size_t)g * m + i] = trace_entry(d);
 }
 
 // Sub-block totals of one stream item: [offspring][chunk][sub-block].
@@ -188,7 +250,9 @@ __device__ __forceinline__ void stream_item(const GenParams &p, int tile, int i0
     const float *src = p.pool + (int64_t)sel.x * p.n_pad;
     float *dst = p.pool + (int64_t)sel.y * p.n_pad;
     const SigT *ra = sig + (int64_t)sel.z * p.n_pad;
-    const SigT *rb = sig + (int64_t)sel.w * p.n_pad;
+    const int w = sel.w;                  // rt2, or -1 - second parent row
+    const bool cross = w < 0;
+    const SigT *rb = sig + (int64_t)(cross ? 0 : w) * p.n_pad;
     const float step = ms;
     if (k + 1 < cnt) {
       sel = __ldcg(p.sel + i0 + k + 1);
@@ -199,7 +263,12 @@ __device__ __forceinline__ void stream_item(const GenParams &p, int tile, int i0
       // chunk v: sub-block = warp, 4 consecutive cases per lane
       const int64_t j0 = base + v * 1024 + tid * 4;
       float str = 0.f, ste = 0.f;
-      if (j0 < p.n_pad) mutate4<SigT>(p, src, dst, ra, rb, j0, step, str, ste);
+      if (j0 < p.n_pad) {
+        if (cross)   // uniform across the CTA: one offspring at a time
+          crossover4<SigT>(p, src, p.pool + (int64_t)(-1 - w) * p.n_pad, dst, ra, j0, str, ste);
+        else
+          mutate4<SigT>(p, src, dst, ra, rb, j0, step, str, ste);
+      }
       const float2 t = subblock_sum(str, ste);
       if (lane == 0) sum[k][v][warp] = t;
     }

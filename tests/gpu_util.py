@@ -37,7 +37,7 @@ def gpu_run(w: W.Workload, data=None, **over):
         tournament_size=p.tournament_size, elitism=int(p.elitism),
         p_grow_function=p.p_grow, p_feature_given_terminal=p.p_feature,
         sigma_dtype=pkg.SIGMA_BF16 if p.sigma_bf16 else pkg.SIGMA_F32,
-        init_mode=p.init_mode, max_genes=p.max_genes)
+        init_mode=p.init_mode, max_genes=p.max_genes, p_crossover=p.p_crossover)
     cfg.stream = torch.cuda.current_stream().cuda_stream
     run = pkg.Run(cfg)
     if data is None:
