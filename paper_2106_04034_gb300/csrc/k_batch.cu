@@ -37,7 +37,7 @@ __device__ __forceinline__ int advance_run(const int *off, int r, int x) {
   return r;
 }
 
-template <typename SigT, int VEC, int OPB>
+template <typename SigT, int VEC, int OPB, bool CROSS>
 __global__ void __launch_bounds__(kGenThreads, 4) batch_kernel(const __grid_constant__ BatchArgs a) {
   constexpr int NW = kGenThreads / 32;
   __shared__ ItemSums<VEC, OPB> s_sum[2];
@@ -58,7 +58,7 @@ __global__ void __launch_bounds__(kGenThreads, 4) batch_kernel(const __grid_cons
       for (int gi = b * kGenThreads + tid; gi < M; gi += nb * kGenThreads) {
         r = advance_run(a.m_off, r, gi);
         const GenParams &p = a.runs[r];
-        select_offspring(p, gi - a.m_off[r], __ldcg(&p.state->gen), __ldcg(&p.state->parity));
+        select_offspring<CROSS>(p, gi - a.m_off[r], __ldcg(&p.state->gen), __ldcg(&p.state->parity));
       }
     }
     if (!grid_sync(gs, epoch, &s_ok)) return;
@@ -89,7 +89,7 @@ __global__ void __launch_bounds__(kGenThreads, 4) batch_kernel(const __grid_cons
         const int4 sel = sel_next;
         const float ms = ms_next;
         if (item + nb < items) prefetch(item + nb);
-        stream_item<SigT, VEC, OPB>(p, tile, i0, cnt, sel, ms, s_sum[buf]);
+        stream_item<SigT, VEC, OPB, CROSS>(p, tile, i0, cnt, sel, ms, s_sum[buf]);
         __syncthreads();   // one barrier per item (s_sum is double-buffered)
         item_partials<VEC, OPB>(p, tile, i0, cnt, s_sum[buf]);
       }
@@ -125,14 +125,16 @@ __global__ void __launch_bounds__(kGenThreads, 4) batch_kernel(const __grid_cons
 }
 
 template <typename SigT, int VEC, int OPB>
-static const void *batch_fn() {
-  return reinterpret_cast<const void *>(&batch_kernel<SigT, VEC, OPB>);
+static const void *batch_fn(bool cross) {
+  return cross ? reinterpret_cast<const void *>(&batch_kernel<SigT, VEC, OPB, true>)
+               : reinterpret_cast<const void *>(&batch_kernel<SigT, VEC, OPB, false>);
 }
 
-static const void *batch_pick(int sigma_bf16, const GenShape &sh) {
+// The crossover variant when any run of the launch has p_crossover > 0.
+static const void *batch_pick(int sigma_bf16, const GenShape &sh, bool cross = false) {
 #define GSGP_BATCH_CASE(V, O)                                                        \
   if (sh.vec == V && sh.opb == O)                                                    \
-    return sigma_bf16 ? batch_fn<__nv_bfloat16, V, O>() : batch_fn<float, V, O>();
+    return sigma_bf16 ? batch_fn<__nv_bfloat16, V, O>(cross) : batch_fn<float, V, O>(cross);
   GSGP_BATCH_CASE(1, 1)
   GSGP_BATCH_CASE(1, 2)
   GSGP_BATCH_CASE(1, 4)
@@ -145,25 +147,33 @@ static const void *batch_pick(int sigma_bf16, const GenShape &sh) {
 
 bool batch_shape_supported(const GenShape &sh) { return batch_pick(0, sh) != nullptr; }
 
+// Co-resident CTAs of both variants (the smaller, should they differ).
 int batch_max_grid(int sigma_bf16, const GenShape &sh) {
-  const void *fn = batch_pick(sigma_bf16, sh);
-  if (!fn) return 0;
-  int dev = 0, coop = 0, sms = 0, per_sm = 0;
+  if (!batch_pick(sigma_bf16, sh)) return 0;
+  int dev = 0, coop = 0, sms = 0, per_sm = 1 << 30;
   if (cudaGetDevice(&dev) != cudaSuccess) return 0;
   if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess || !coop)
     return 0;
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kGenThreads, 0) != cudaSuccess) {
-    cudaGetLastError();
-    return 0;
+  for (const bool cross : {false, true}) {
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_pick(sigma_bf16, sh, cross),
+                                                      kGenThreads, 0) != cudaSuccess) {
+      cudaGetLastError();
+      return 0;
+    }
+    per_sm = n < per_sm ? n : per_sm;
   }
   return per_sm * sms;
 }
 
 cudaError_t launch_batch(const BatchArgs &a, int sigma_bf16, const GenShape &sh, int grid,
                          cudaStream_t s) {
-  const void *fn = batch_pick(sigma_bf16, sh);
-  if (!fn || grid <= 0 || a.R < 1 || a.R > kBatchRunsPerLaunch) return cudaErrorInvalidValue;
+  if (a.R < 1 || a.R > kBatchRunsPerLaunch) return cudaErrorInvalidValue;
+  bool cross = false;
+  for (int r = 0; r < a.R; ++r) cross |= a.runs[r].p_crossover > 0.0f;
+  const void *fn = batch_pick(sigma_bf16, sh, cross);
+  if (!fn || grid <= 0) return cudaErrorInvalidValue;
   void *args[] = {const_cast<BatchArgs *>(&a)};
   return cudaLaunchCooperativeKernel(fn, dim3((unsigned)grid), dim3(kGenThreads), args, 0, s);
 }

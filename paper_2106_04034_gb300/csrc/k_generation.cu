@@ -52,7 +52,7 @@ __global__ void __launch_bounds__(kSelectThreads) select_kernel(const GenParams 
   griddep_launch();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= p.m) return;
-  select_offspring(p, i, __ldcg(&p.state->gen), __ldcg(&p.state->parity));
+  select_offspring<true>(p, i, __ldcg(&p.state->gen), __ldcg(&p.state->parity));
 }
 
 // ------------------------------------------------------------- stream -----
@@ -65,7 +65,7 @@ __global__ void __launch_bounds__(kGenThreads) stream_kernel(const GenParams p) 
   const int tile = blockIdx.x / groups;
   const int i0 = (blockIdx.x - tile * groups) * OPB;
   const int cnt = min(OPB, p.m - i0);
-  stream_item<SigT, VEC, OPB>(p, tile, i0, cnt, __ldcg(p.sel + i0), __ldcg(p.sel_ms + i0), s_sum);
+  stream_item<SigT, VEC, OPB, true>(p, tile, i0, cnt, __ldcg(p.sel + i0), __ldcg(p.sel_ms + i0), s_sum);
   __syncthreads();
   item_partials<VEC, OPB>(p, tile, i0, cnt, s_sum);
 }

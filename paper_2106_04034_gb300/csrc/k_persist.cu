@@ -106,6 +106,7 @@ struct GenState {
 
 // S: tournament selection and mutation draws; offspring i is drawn by thread
 // i % 256 of CTA i / 256.
+template <bool CROSS>
 __device__ __forceinline__ void select_phase(const GenParams &p, const GenState &pd, int b,
                                              int nb) {
   const int m = p.m;
@@ -120,7 +121,7 @@ __device__ __forceinline__ void select_phase(const GenParams &p, const GenState 
       orow = (pd.elite && i == pd.bP) ? __ldcg(pm + m + pd.w) : __ldcg(pm + i);
     else
       orow = __ldcg(pm + m + i);
-    const Draws d = draw_offspring(
+    const Draws d = draw_offspring<CROSS>(
         p, i, g,
         [&](int s) { return (pd.active && pd.elite && s == pd.w) ? pd.fbp : __ldcg(F + s); },
         [&](int s) {
@@ -257,7 +258,7 @@ __device__ __forceinline__ void survive_phase(const GenParams &p, const PersistA
   __syncthreads();
 }
 
-template <typename SigT, int VEC, int OPB>
+template <typename SigT, int VEC, int OPB, bool CROSS>
 __global__ void __launch_bounds__(kGenThreads, 4) persist_kernel(const GenParams p, PersistArgs x) {
   constexpr int NW = kGenThreads / 32;
   constexpr int W = 1024 * VEC;
@@ -290,7 +291,7 @@ __global__ void __launch_bounds__(kGenThreads, 4) persist_kernel(const GenParams
 
   for (int it = 0; it < x.G; ++it) {
     // ---------------- S: selection ----------------------------------------
-    select_phase(p, st, b, nb);
+    select_phase<CROSS>(p, st, b, nb);
     if (!grid_sync(gs, epoch, &s_ok)) return;
 
     // ---------------- M: mutation stream ----------------------------------
@@ -317,7 +318,7 @@ __global__ void __launch_bounds__(kGenThreads, 4) persist_kernel(const GenParams
           sel_next = __ldcg(p.sel + i0n);
           ms_next = __ldcg(p.sel_ms + i0n);
         }
-        stream_item<SigT, VEC, OPB>(p, tile, i0, cnt, sel, ms, s_sum[buf]);
+        stream_item<SigT, VEC, OPB, CROSS>(p, tile, i0, cnt, sel, ms, s_sum[buf]);
         // one barrier per item; the other buffer is written by the next item,
         // and this one again only after the next item's barrier
         __syncthreads();
@@ -470,7 +471,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1) persist_tma_kernel(const GenPa
   __syncthreads();
 
   for (int it = 0; it < x.G; ++it) {
-    select_phase(p, st, b, nb);
+    select_phase<false>(p, st, b, nb);
     if (!grid_sync(gs, epoch, &s_ok)) return;
 
     // ---------------- M: TMA-staged mutation stream -----------------------
@@ -639,8 +640,9 @@ __global__ void __launch_bounds__(kTmaThreads, 1) persist_tma_kernel(const GenPa
 }
 
 template <typename SigT, int VEC, int OPB>
-static const void *persist_fn() {
-  return reinterpret_cast<const void *>(&persist_kernel<SigT, VEC, OPB>);
+static const void *persist_fn(bool cross) {
+  return cross ? reinterpret_cast<const void *>(&persist_kernel<SigT, VEC, OPB, true>)
+               : reinterpret_cast<const void *>(&persist_kernel<SigT, VEC, OPB, false>);
 }
 
 template <typename SigT, int VEC>
@@ -656,10 +658,12 @@ struct PersistKernel {
   int smem;
 };
 
-static PersistKernel pick(int bf, const GenShape &sh) {
+// cross: the register-stream variant with crossover (the TMA variant has none).
+static PersistKernel pick(int bf, const GenShape &sh, bool cross = false) {
 #define GSGP_P(V, O)                                                                      \
   if (sh.vec == V && sh.opb == O)                                                         \
-    return {bf ? persist_fn<__nv_bfloat16, V, O>() : persist_fn<float, V, O>(), kGenThreads, 0};
+    return {bf ? persist_fn<__nv_bfloat16, V, O>(cross) : persist_fn<float, V, O>(cross), \
+            kGenThreads, 0};
   GSGP_P(1, 1) GSGP_P(1, 2) GSGP_P(1, 4) GSGP_P(2, 1) GSGP_P(2, 2) GSGP_P(2, 4)
 #undef GSGP_P
 #define GSGP_T(V)                                                                             \
@@ -667,7 +671,9 @@ static PersistKernel pick(int bf, const GenShape &sh) {
     return bf ? PersistKernel{persist_tma_fn<__nv_bfloat16, V>(), kTmaThreads,                \
                               TmaCfg<__nv_bfloat16, V>::kSmem}                                \
               : PersistKernel{persist_tma_fn<float, V>(), kTmaThreads, TmaCfg<float, V>::kSmem};
-  GSGP_T(1) GSGP_T(2) GSGP_T(4)
+  if (!cross) {
+    GSGP_T(1) GSGP_T(2) GSGP_T(4)
+  }
 #undef GSGP_T
   return {nullptr, 0, 0};
 }
@@ -677,6 +683,8 @@ bool persist_shape_supported(const GenShape &sh) {
   return (sh.vec == 1 || sh.vec == 2) && (sh.opb == 1 || sh.opb == 2 || sh.opb == 4);
 }
 
+// Co-resident CTAs; for the register stream the smaller of the two variants
+// (with and without crossover), should they differ.
 int persist_max_grid(int sigma_bf16, const GenShape &sh) {
   const PersistKernel k = pick(sigma_bf16, sh);
   if (!k.fn) return 0;
@@ -691,12 +699,19 @@ int persist_max_grid(int sigma_bf16, const GenShape &sh) {
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k.fn, k.threads, k.smem) !=
       cudaSuccess)
     return 0;
+  if (sh.opb > 0) {
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, pick(sigma_bf16, sh, true).fn, k.threads,
+                                                      k.smem) != cudaSuccess)
+      return 0;
+    per_sm = n < per_sm ? n : per_sm;
+  }
   return per_sm * sms;
 }
 
 cudaError_t launch_persist(const GenParams &p, const PersistArgs &x, int sigma_bf16,
                            const GenShape &sh, int grid, cudaStream_t s) {
-  const PersistKernel k = pick(sigma_bf16, sh);
+  const PersistKernel k = pick(sigma_bf16, sh, p.p_crossover > 0.0f);
   if (!k.fn || grid <= 0) return cudaErrorInvalidValue;
   if (k.smem > 0) {
     const cudaError_t e =

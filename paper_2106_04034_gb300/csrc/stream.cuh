@@ -96,7 +96,8 @@ __device__ __forceinline__ void tournament(const GenParams &p, int i, WordStream
   }
 }
 
-template <typename FitFn, typename RowFn>
+// CROSS = false compiles the mutation-only draws (p_crossover must be 0).
+template <bool CROSS, typename FitFn, typename RowFn>
 __device__ __forceinline__ Draws draw_offspring(const GenParams &p, int i, int g, FitFn fit,
                                                 RowFn row) {
   WordStream ws(p.key, (uint32_t)i, (uint32_t)g, p.run);
@@ -113,7 +114,7 @@ __device__ __forceinline__ Draws draw_offspring(const GenParams &p, int i, int g
   d.cross = false;
   d.parent2 = d.parent;
   d.prow2 = d.prow;
-  if (p.p_crossover > 0.0f) {
+  if (CROSS && p.p_crossover > 0.0f) {
     d.cross = draw_u24(ws.next()) < p.p_crossover;
     if (d.cross) tournament(p, i, ws, fit, row, d.parent2, d.prow2);
   }
@@ -217,12 +218,13 @@ __device__ __forceinline__ double2 chunk_total(const float2 *sub) {
 // and the draws of "GSM"): writes the draws used by the stream (parent row,
 // offspring row, rt1, rt2, step) and the trace entry (parent slot, rt1, rt2,
 // step bits).
+template <bool CROSS>
 __device__ __forceinline__ void select_offspring(const GenParams &p, int i, int g, int par) {
   const int m = p.m;
   const double *F = p.fit + (size_t)par * m;
   const int *perm = p.perm + (size_t)par * 2 * m;
   const int orow = __ldcg(perm + m + i);
-  const Draws d = draw_offspring(
+  const Draws d = draw_offspring<CROSS>(
       p, i, g, [&](int slot) { return __ldcg(F + slot); },
       [&](int slot) { return __ldcg(perm + slot); });
   p.sel[i] = sel_entry(d, orow);
@@ -240,7 +242,8 @@ using ItemSums = float2[OPB][VEC][kGenThreads / 32];
 // those of the next offspring are loaded while the current one streams.
 // Warp w leaves the total of sub-block w of chunk v of offspring k in
 // sum[k][v][w]; after a barrier item_partials finishes the chunk sums.
-template <typename SigT, int VEC, int OPB>
+// CROSS = false compiles the mutation stream alone.
+template <typename SigT, int VEC, int OPB, bool CROSS>
 __device__ __forceinline__ void stream_item(const GenParams &p, int tile, int i0, int cnt,
                                             int4 sel, float ms, ItemSums<VEC, OPB> &sum) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -251,7 +254,7 @@ __device__ __forceinline__ void stream_item(const GenParams &p, int tile, int i0
     float *dst = p.pool + (int64_t)sel.y * p.n_pad;
     const SigT *ra = sig + (int64_t)sel.z * p.n_pad;
     const int w = sel.w;                  // rt2, or -1 - second parent row
-    const bool cross = w < 0;
+    const bool cross = CROSS && w < 0;
     const SigT *rb = sig + (int64_t)(cross ? 0 : w) * p.n_pad;
     const float step = ms;
     if (k + 1 < cnt) {
