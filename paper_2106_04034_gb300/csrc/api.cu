@@ -505,6 +505,79 @@ extern "C" gsgp_status gsgp_init(gsgp_ctx *c) {
                              cf.const_lo, cf.const_hi, c->R_genes, c->R_consts, c->R_len,
                              c->stream));
   }
+  // the interpreter runs the programs with their "terminal, function" pairs
+  // fused, from buffers that live for this call
+  struct Fused {
+    gsgp_ctx *c;
+    int *genes[2] = {nullptr, nullptr}, *len[2] = {nullptr, nullptr};
+    float *consts[2] = {nullptr, nullptr};
+    int *need = nullptr, *order = nullptr;
+    ~Fused() {
+      for (int q = 0; q < 2; ++q) {
+        dfree(c, genes[q]);
+        dfree(c, consts[q]);
+        dfree(c, len[q]);
+      }
+      dfree(c, need);
+      dfree(c, order);
+    }
+  } fz{c};
+  for (int q = 0; q < 2; ++q) {
+    const size_t cnt = q == 0 ? (size_t)m : (size_t)r, K = q == 0 ? (size_t)Kp : (size_t)Kr;
+    TRY(dalloc_n(c, &fz.genes[q], cnt * K));
+    TRY(dalloc_n(c, &fz.consts[q], cnt * K));
+    TRY(dalloc_n(c, &fz.len[q], cnt));
+  }
+  LAUNCH(1, launch_fuse(prog_genes(c, true), prog_consts(c, true), prog_len(c, true), m, Kp,
+                        fz.genes[0], fz.consts[0], fz.len[0], c->stream));
+  LAUNCH(1, launch_fuse(prog_genes(c, false), prog_consts(c, false), prog_len(c, false), r, Kr,
+                        fz.genes[1], fz.consts[1], fz.len[1], c->stream));
+  // Interpreter launches: one per group of programs, shared memory sized for
+  // the group's deepest stack.  Linear genomes are grouped by the stack
+  // entries each needs (most need a few; the deepest of a large pool needs
+  // about twice as many, and sizing every CTA for it costs occupancy); a
+  // pool of trees is one group sized by its depth.
+  struct Group {
+    int first, count, slots;   // first < 0: programs 0 .. count - 1 in order
+  };
+  std::vector<Group> groups[2];
+  if (linear) {
+    TRY(dalloc_n(c, &fz.need, (size_t)(m + r)));
+    TRY(dalloc_n(c, &fz.order, (size_t)(m + r)));
+    LAUNCH(1, launch_stack_need(fz.genes[0], fz.len[0], m, Kp, fz.need, c->stream));
+    LAUNCH(1, launch_stack_need(fz.genes[1], fz.len[1], r, Kr, fz.need + m, c->stream));
+    std::vector<int> need((size_t)(m + r)), order;
+    order.reserve((size_t)(m + r));
+    CK(cudaMemcpyAsync(need.data(), fz.need, sizeof(int) * need.size(), cudaMemcpyDeviceToHost,
+                       c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    static const int kSlotBounds[] = {2, 4, 6, 8, 12, 16, 24, kMaxStack};
+    for (int q = 0; q < 2; ++q) {
+      const int base = q == 0 ? 0 : m, cnt = q == 0 ? m : r;
+      int lo = -1;
+      for (const int hi : kSlotBounds) {
+        Group gq{(int)order.size(), 0, 1};
+        for (int i = 0; i < cnt; ++i) {
+          const int v = need[(size_t)(base + i)];
+          if (v > lo && v <= hi) {
+            order.push_back(i);
+            gq.slots = v > gq.slots ? v : gq.slots;
+          }
+        }
+        gq.count = (int)order.size() - gq.first;
+        if (gq.count > 0) groups[q].push_back(gq);
+        lo = hi;
+      }
+    }
+    if ((int)order.size() != m + r)
+      return fail(c, GSGP_E_INVALID, "interpreter groups cover %d of %d programs",
+                  (int)order.size(), m + r);
+    CK(cudaMemcpyAsync(fz.order, order.data(), sizeof(int) * order.size(), cudaMemcpyHostToDevice,
+                       c->stream));
+  } else {
+    groups[0].push_back(Group{-1, m, slots_p});
+    groups[1].push_back(Group{-1, r, slots_r});
+  }
   InterpParams ip{};
   ip.X = c->X;
   ip.target = c->t;
@@ -514,31 +587,37 @@ extern "C" gsgp_status gsgp_init(gsgp_ctx *c) {
   ip.tiles = c->tiles_interp;
   ip.protect_eps = cf.protect_eps;
   // population semantics + squared errors (rows 0..m-1 of the pool)
-  ip.genes = prog_genes(c, true);
-  ip.consts = prog_consts(c, true);
-  ip.lengths = prog_len(c, true);
+  ip.genes = fz.genes[0];
+  ip.consts = fz.consts[0];
+  ip.lengths = fz.len[0];
   ip.K = Kp;
   ip.max_len = max_len_p;
-  ip.stack_slots = slots_p;
   ip.out = c->pool;
   ip.partial = c->partial;
   c->init_timed = false;
   if (c->timing && !c->ev_init[0])
     for (auto &e : c->ev_init) CK(cudaEventCreate(&e));
   if (c->timing) CK(cudaEventRecord(c->ev_init[0], c->stream));
-  LAUNCH(1, launch_interpret(0, ip, m, c->stream));
+  for (const Group &gq : groups[0]) {
+    ip.order = gq.first < 0 ? nullptr : fz.order + gq.first;
+    ip.stack_slots = gq.slots;
+    LAUNCH(1, launch_interpret(0, ip, gq.count, c->stream));
+  }
   if (c->timing) CK(cudaEventRecord(c->ev_init[1], c->stream));
   // random-tree semantics wrapped by the logistic function
-  ip.genes = prog_genes(c, false);
-  ip.consts = prog_consts(c, false);
-  ip.lengths = prog_len(c, false);
+  ip.genes = fz.genes[1];
+  ip.consts = fz.consts[1];
+  ip.lengths = fz.len[1];
   ip.K = Kr;
   ip.max_len = max_len_r;
-  ip.stack_slots = slots_r;
   ip.out = c->sigR;
   ip.partial = nullptr;
   if (c->timing) CK(cudaEventRecord(c->ev_init[2], c->stream));
-  LAUNCH(1, launch_interpret(cf.sigma_dtype == GSGP_SIGMA_BF16 ? 2 : 1, ip, r, c->stream));
+  for (const Group &gq : groups[1]) {
+    ip.order = gq.first < 0 ? nullptr : fz.order + gq.first;
+    ip.stack_slots = gq.slots;
+    LAUNCH(1, launch_interpret(cf.sigma_dtype == GSGP_SIGMA_BF16 ? 2 : 1, ip, gq.count, c->stream));
+  }
   if (c->timing) {
     CK(cudaEventRecord(c->ev_init[3], c->stream));
     c->init_timed = true;

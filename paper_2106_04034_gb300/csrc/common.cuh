@@ -12,6 +12,10 @@ namespace gsgp {
 // ---- gene encoding (linear postfix genome, Sec. 2.2 "Initialization") ----
 constexpr int kOpAdd = 0, kOpSub = 1, kOpMul = 2, kOpDiv = 3, kOpConst = 4, kOpVar = 5;
 constexpr int kGenePad = -1;
+// Interpreter-only codes written by the terminal-operand fusion pass: a
+// terminal and the function right after it as one gene, base + function
+// (the feature index in the upper bits as for kOpVar).
+constexpr int kOpFusedConst = 8, kOpFusedVar = 12;
 constexpr int kMaxDepth = 10;                    // deepest tree a pool may hold
 constexpr int kMaxGenes = (1 << (kMaxDepth + 1)) - 1;
 constexpr int kMaxGenomeGenes = 4095;             // longest linear genome
@@ -129,6 +133,7 @@ struct InterpParams {
   int tiles;
   int stack_slots;           // shared-memory stack depth below the cached top
   float protect_eps;
+  const int *order;          // programs of this launch (CTA column x runs order[x]), or null
 };
 
 }  // namespace gsgp

@@ -224,6 +224,102 @@ cudaError_t launch_compact(const int *genes, const float *consts, const int *len
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// Terminal-operand fusion.  In postfix code a terminal followed by a
+// function pushes the terminal and at once pops it again as the function's
+// right operand; the pair is one step, "stack top := f(stack top, terminal)".
+// Each such pair becomes one gene (kOpFusedConst / kOpFusedVar + f, with the
+// terminal's feature index or constant), which spares the interpreter a
+// dispatch and a shared-memory push and pop per pair.  The arithmetic is
+// unchanged: the same operation on the same two operands.  On an empty
+// stack the interpreter pushes the terminal and skips the function, as the
+// unfused pair would.  One warp per program: lanes take 32 consecutive
+// genes and place the kept ones by ballot.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ bool gene_is_terminal(int g) {
+  return (g & 0xFF) == kOpConst || (g & 0xFF) == kOpVar;
+}
+__device__ __forceinline__ bool gene_is_function(int g) { return g >= 0 && (g & 0xFF) < kOpConst; }
+
+__global__ void __launch_bounds__(128)
+    fuse_kernel(const int *__restrict__ genes, const float *__restrict__ consts,
+                const int *__restrict__ lengths, int count, int K, int *__restrict__ out_genes,
+                float *__restrict__ out_consts, int *__restrict__ out_len) {
+  const int prog = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (prog >= count) return;   // whole warps leave together
+  const int *g = genes + (size_t)prog * K;
+  const float *c = consts + (size_t)prog * K;
+  int *og = out_genes + (size_t)prog * K;
+  float *oc = out_consts + (size_t)prog * K;
+  const int len = lengths[prog];
+  int n = 0;
+  for (int k0 = 0; k0 < len; k0 += 32) {
+    const int k = k0 + lane;
+    const bool in = k < len;
+    const int gk = in ? g[k] : kGenePad;
+    const int gnext = k + 1 < len ? g[k + 1] : kGenePad;
+    const int gprev = in && k > 0 ? g[k - 1] : kGenePad;
+    const bool drop = gene_is_terminal(gk) && gene_is_function(gnext);   // joins gene k + 1
+    const bool fused = gene_is_function(gk) && gene_is_terminal(gprev);
+    const unsigned keep = __ballot_sync(0xffffffffu, in && !drop);
+    if (in && !drop) {
+      const int pos = n + __popc(keep & ((1u << lane) - 1u));
+      if (fused) {
+        const int base = (gprev & 0xFF) == kOpVar ? kOpFusedVar : kOpFusedConst;
+        og[pos] = (gprev & ~0xFF) | (base + (gk & 0xFF));
+        oc[pos] = c[k - 1];
+      } else {
+        og[pos] = gk;
+        oc[pos] = c[k];
+      }
+    }
+    n += __popc(keep);
+  }
+  if (lane == 0) out_len[prog] = n;
+}
+
+cudaError_t launch_fuse(const int *genes, const float *consts, const int *lengths, int count,
+                        int K, int *out_genes, float *out_consts, int *out_len, cudaStream_t s) {
+  if (count <= 0) return cudaSuccess;
+  fuse_kernel<<<(unsigned)((count + 3) / 4), 128, 0, s>>>(genes, consts, lengths, count, K,
+                                                         out_genes, out_consts, out_len);
+  return cudaGetLastError();
+}
+
+// Shared-memory stack entries one fused program needs: the deepest stack
+// it reaches under the interpreter's rules (a fused gene on a non-empty
+// stack pushes nothing, a function short of operands is skipped) less the
+// top, which lives in registers.  The interpreter groups programs by this
+// need so that shallow programs run at a higher occupancy.
+__global__ void __launch_bounds__(256)
+    stack_need_kernel(const int *__restrict__ genes, const int *__restrict__ lengths, int count,
+                      int K, int *__restrict__ need) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= count) return;
+  const int *g = genes + (size_t)i * K;
+  const int len = lengths[i];
+  int sp = 0, best = 0;
+  for (int k = 0; k < len; ++k) {
+    const int op = g[k] & 0xFF;
+    if (op >= kOpFusedConst && sp >= 1) continue;
+    if (op >= kOpConst) {
+      ++sp;
+      best = max(best, sp);
+    } else if (sp >= 2) {
+      --sp;
+    }
+  }
+  need[i] = best > 1 ? best - 1 : 0;
+}
+
+cudaError_t launch_stack_need(const int *genes, const int *lengths, int count, int K, int *need,
+                              cudaStream_t s) {
+  if (count <= 0) return cudaSuccess;
+  stack_need_kernel<<<(count + 255) / 256, 256, 0, s>>>(genes, lengths, count, K, need);
+  return cudaGetLastError();
+}
+
 // Deepest stack any program of a pool reaches under the interpreter's rule
 // (a function short of operands is skipped): sizes the interpreter's shared
 // memory stack.  One thread per program; *out must be zero before.
@@ -308,6 +404,9 @@ cudaError_t launch_nonfinite_check(const float *v, int64_t n, unsigned *flag, cu
 // row), so the gene stream is uniform across the CTA and decoded once per
 // 4 cases.  The top of the stack lives in registers; deeper entries live in
 // shared memory laid out [slot][thread] (conflict-free 16-byte accesses).
+// The programs arrive with their "terminal, function" pairs fused
+// (fuse_kernel), which apply the function to the top and the terminal
+// without touching shared memory.
 // A function with fewer than two operands on the stack is skipped and the
 // value is register Out, the last function output (the paper's rules; a
 // ramped half-and-half program never skips and ends with its root).  Protected division
@@ -338,7 +437,7 @@ __global__ void __launch_bounds__(kInterpThreads) interpret_kernel(InterpParams 
   float *s_const = reinterpret_cast<float *>(s_gene + p.max_len);
   __shared__ float2 s_sub[kInterpThreads / 32];   // sub-block (warp) totals
 
-  const int prog = blockIdx.x;
+  const int prog = p.order ? p.order[blockIdx.x] : (int)blockIdx.x;
   const int tile = blockIdx.y;
   const int tid = threadIdx.x;
   const int len = p.lengths[prog];
@@ -356,17 +455,25 @@ __global__ void __launch_bounds__(kInterpThreads) interpret_kernel(InterpParams 
   for (int k = 0; k < len; ++k) {
     const int g = s_gene[k];
     const int op = g & 0xFF;
-    if (op >= kOpConst) {
+    if (op >= kOpConst) {   // a terminal, alone or fused with the function after it
       float4 v;
-      if (op == kOpVar) {
+      if (op == kOpVar || op >= kOpFusedVar) {
         v = __ldg(reinterpret_cast<const float4 *>(p.X + (int64_t)(g >> 8) * p.n_pad) + jj);
       } else {
         const float c = s_const[k];
         v = make_float4(c, c, c, c);
       }
-      if (sp > 0 && sp - 1 < p.stack_slots) s_stack[(sp - 1) * kInterpThreads + tid] = tos;
-      tos = v;
-      ++sp;
+      if (op >= kOpFusedConst && sp >= 1) {   // f(stack top, terminal), no push or pop
+        const int f = op & 3;
+        tos.x = apply_op(f, tos.x, v.x, p.protect_eps);
+        tos.y = apply_op(f, tos.y, v.y, p.protect_eps);
+        tos.z = apply_op(f, tos.z, v.z, p.protect_eps);
+        tos.w = apply_op(f, tos.w, v.w, p.protect_eps);
+      } else {
+        if (sp > 0 && sp - 1 < p.stack_slots) s_stack[(sp - 1) * kInterpThreads + tid] = tos;
+        tos = v;
+        ++sp;
+      }
     } else if (sp >= 2) {
       const float4 a = s_stack[(sp - 2) * kInterpThreads + tid];
       tos.x = apply_op(op, a.x, tos.x, p.protect_eps);

@@ -26,6 +26,15 @@ cudaError_t launch_compact(const int *genes, const float *consts, const int *len
                            int K, int *out_genes, float *out_consts, int *out_len,
                            cudaStream_t s);
 
+// Each "terminal, function" pair of a postfix program as one fused gene
+// (kOpFusedConst / kOpFusedVar + function): the form the interpreter runs.
+cudaError_t launch_fuse(const int *genes, const float *consts, const int *lengths, int count,
+                        int K, int *out_genes, float *out_consts, int *out_len, cudaStream_t s);
+
+// Stack entries each fused program needs below the cached top (need[i]).
+cudaError_t launch_stack_need(const int *genes, const int *lengths, int count, int K, int *need,
+                              cudaStream_t s);
+
 cudaError_t launch_transpose(const float *in, int64_t n, int l, float *out, int64_t n_pad,
                              int64_t col0, cudaStream_t s);
 

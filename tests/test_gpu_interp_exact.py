@@ -1,0 +1,78 @@
+"""The interpreter's arithmetic, bit for bit.  Every operation of a program
+is one IEEE float32 operation (protected division: 1 where |b| < eps), so a
+float32 evaluation of the program as generated (skip rule and register Out
+for linear genomes) gives the same bits case by case.  The GPU runs the
+programs in another form (live code of genomes, "terminal, function" pairs
+fused); this checks that the form changes no arithmetic."""
+import numpy as np
+import pytest
+
+import workloads as W
+from gpu_util import gpu_run
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+import paper_2106_04034_gb300 as pkg  # noqa: E402
+
+
+def f32_program(genes, consts, X, eps):
+    """Float32 value of one program on the cases X (features, n): a stack
+    machine with the skip rule and the Out register."""
+    n = X.shape[1]
+    stack, out = [], None
+    with np.errstate(all="ignore"):
+        for g, c in zip(genes, consts):
+            g = int(g)
+            if g == -1:
+                break
+            op = g & 0xFF
+            if op == 5:
+                stack.append(X[g >> 8])
+            elif op == 4:
+                stack.append(np.full(n, c, np.float32))
+            elif len(stack) >= 2:
+                b = stack.pop()
+                a = stack.pop()
+                if op == 0:
+                    r = a + b
+                elif op == 1:
+                    r = a - b
+                elif op == 2:
+                    r = a * b
+                else:
+                    r = np.where(np.abs(b) < eps, np.float32(1), a / b)
+                r = r.astype(np.float32)
+                stack.append(r)
+                out = r
+    if out is not None:
+        return out
+    return stack[-1] if stack else np.zeros(n, np.float32)
+
+
+CASES = {
+    "trees": W.TINY,
+    "deep trees": W.TINY.replace(name="deep trees", pop_size=96, n_random_trees=32,
+                                 pop_min_depth=2, pop_max_depth=8, n_train=900, n_test=300),
+    "genomes k127": W.TINY.replace(name="genomes", init_mode=1, max_genes=127),
+    "genomes k1023": W.TINY.replace(name="long genomes", init_mode=1, max_genes=1023,
+                                    pop_size=48, n_random_trees=16),
+}
+
+
+@pytest.mark.parametrize("case", list(CASES))
+def test_population_semantics_bit_exact(case):
+    w = CASES[case]
+    run, data, p = gpu_run(w)
+    X = np.ascontiguousarray(np.concatenate([data[0], data[2]]).T, dtype=np.float32)
+    eps = np.float32(p.protect_eps)
+    g, c, L = run.programs(pkg.POOL_POPULATION)
+    S = run.semantics(pkg.POOL_POPULATION)
+    for i in range(len(L)):
+        want = f32_program(g[i, :L[i]], c[i, :L[i]], X, eps)
+        assert np.array_equal(S[i].view(np.uint32), want.view(np.uint32)) or \
+            np.array_equal(S[i], want, equal_nan=True), i
+    run.close()
