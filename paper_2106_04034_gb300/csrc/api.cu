@@ -586,6 +586,7 @@ extern "C" gsgp_status gsgp_init(gsgp_ctx *c) {
   ip.n_cases = (int)c->N;
   ip.tiles = c->tiles_interp;
   ip.protect_eps = cf.protect_eps;
+  ip.n_features = c->l;
   // population semantics + squared errors (rows 0..m-1 of the pool)
   ip.genes = fz.genes[0];
   ip.consts = fz.consts[0];

@@ -134,6 +134,7 @@ struct InterpParams {
   int stack_slots;           // shared-memory stack depth below the cached top
   float protect_eps;
   const int *order;          // programs of this launch (CTA column x runs order[x]), or null
+  int n_features;            // rows of X
 };
 
 }  // namespace gsgp

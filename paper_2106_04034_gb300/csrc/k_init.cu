@@ -429,57 +429,73 @@ __device__ __forceinline__ float logistic(float v) { return 1.0f / (1.0f + expf(
 constexpr int kInterpThreads = 256;
 constexpr int kInterpTile = kInterpThreads * 4;
 
+// One operation on four cases, the operator decided once (warp-uniform).
+__device__ __forceinline__ float4 apply4(int f, const float4 a, const float4 b, float eps) {
+  switch (f) {
+    case kOpAdd: return make_float4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w);
+    case kOpSub: return make_float4(a.x - b.x, a.y - b.y, a.z - b.z, a.w - b.w);
+    case kOpMul: return make_float4(a.x * b.x, a.y * b.y, a.z * b.z, a.w * b.w);
+    default:
+      return make_float4(apply_op(kOpDiv, a.x, b.x, eps), apply_op(kOpDiv, a.y, b.y, eps),
+                         apply_op(kOpDiv, a.z, b.z, eps), apply_op(kOpDiv, a.w, b.w, eps));
+  }
+}
+
+// Decoded gene of the interpreter's loop: bits 0-1 the function, bit 2 a
+// terminal operand (alone or fused), bit 3 the terminal is a feature, bit 4
+// a function (alone or fused); the argument is the feature row's offset in
+// float4 units or the constant's bits.
+constexpr int kDecFun = 16, kDecTerm = 4, kDecVar = 8;
+
+__device__ __forceinline__ int2 decode_gene(int g, float c, int64_t row4) {
+  const int op = g & 0xFF;
+  if (op < kOpConst) return make_int2(kDecFun | op, 0);
+  const bool var = op == kOpVar || op >= kOpFusedVar;
+  const int code = kDecTerm | (var ? kDecVar : 0) | (op >= kOpFusedConst ? kDecFun | (op & 3) : 0);
+  return make_int2(code, var ? (int)((g >> 8) * row4) : __float_as_int(c));
+}
+
 template <int MODE>
 __global__ void __launch_bounds__(kInterpThreads) interpret_kernel(InterpParams p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float4 *s_stack = reinterpret_cast<float4 *>(smem_raw);
-  int *s_gene = reinterpret_cast<int *>(s_stack + (size_t)p.stack_slots * kInterpThreads);
-  float *s_const = reinterpret_cast<float *>(s_gene + p.max_len);
+  int2 *s_prog = reinterpret_cast<int2 *>(s_stack + (size_t)p.stack_slots * kInterpThreads);
   __shared__ float2 s_sub[kInterpThreads / 32];   // sub-block (warp) totals
 
   const int prog = p.order ? p.order[blockIdx.x] : (int)blockIdx.x;
   const int tile = blockIdx.y;
   const int tid = threadIdx.x;
   const int len = p.lengths[prog];
-  for (int k = tid; k < len; k += kInterpThreads) {
-    s_gene[k] = p.genes[(size_t)prog * p.K + k];
-    s_const[k] = p.consts[(size_t)prog * p.K + k];
-  }
+  const int64_t row4 = p.n_pad / 4;   // float4s per feature row
+  for (int k = tid; k < len; k += kInterpThreads)
+    s_prog[k] = decode_gene(p.genes[(size_t)prog * p.K + k], p.consts[(size_t)prog * p.K + k], row4);
   __syncthreads();
 
   const int64_t j4 = (int64_t)tile * kInterpThreads + tid;   // float4 index
   const bool valid = j4 * 4 < p.n_pad;
-  const int64_t jj = valid ? j4 : 0;
+  const float4 *xcase = reinterpret_cast<const float4 *>(p.X) + (valid ? j4 : 0);
+  float4 *stk = s_stack + tid;   // this thread's column of the stack
   float4 tos = make_float4(0.f, 0.f, 0.f, 0.f);
   int sp = 0;
   for (int k = 0; k < len; ++k) {
-    const int g = s_gene[k];
-    const int op = g & 0xFF;
-    if (op >= kOpConst) {   // a terminal, alone or fused with the function after it
+    const int2 e = s_prog[k];
+    if (e.x & kDecTerm) {   // a terminal, alone or fused with the function after it
       float4 v;
-      if (op == kOpVar || op >= kOpFusedVar) {
-        v = __ldg(reinterpret_cast<const float4 *>(p.X + (int64_t)(g >> 8) * p.n_pad) + jj);
+      if (e.x & kDecVar) {
+        v = __ldg(xcase + e.y);
       } else {
-        const float c = s_const[k];
+        const float c = __int_as_float(e.y);
         v = make_float4(c, c, c, c);
       }
-      if (op >= kOpFusedConst && sp >= 1) {   // f(stack top, terminal), no push or pop
-        const int f = op & 3;
-        tos.x = apply_op(f, tos.x, v.x, p.protect_eps);
-        tos.y = apply_op(f, tos.y, v.y, p.protect_eps);
-        tos.z = apply_op(f, tos.z, v.z, p.protect_eps);
-        tos.w = apply_op(f, tos.w, v.w, p.protect_eps);
+      if ((e.x & kDecFun) && sp >= 1) {   // f(stack top, terminal), no push or pop
+        tos = apply4(e.x & 3, tos, v, p.protect_eps);
       } else {
-        if (sp > 0 && sp - 1 < p.stack_slots) s_stack[(sp - 1) * kInterpThreads + tid] = tos;
+        if (sp > 0 && sp - 1 < p.stack_slots) stk[(sp - 1) * kInterpThreads] = tos;
         tos = v;
         ++sp;
       }
     } else if (sp >= 2) {
-      const float4 a = s_stack[(sp - 2) * kInterpThreads + tid];
-      tos.x = apply_op(op, a.x, tos.x, p.protect_eps);
-      tos.y = apply_op(op, a.y, tos.y, p.protect_eps);
-      tos.z = apply_op(op, a.z, tos.z, p.protect_eps);
-      tos.w = apply_op(op, a.w, tos.w, p.protect_eps);
+      tos = apply4(e.x & 3, stk[(sp - 2) * kInterpThreads], tos, p.protect_eps);
       --sp;
     }
   }
@@ -529,7 +545,10 @@ __global__ void __launch_bounds__(kInterpThreads) interpret_kernel(InterpParams 
 cudaError_t launch_interpret(int mode, const InterpParams &p, int count, cudaStream_t s) {
   if (count <= 0) return cudaSuccess;
   const size_t smem = (size_t)p.stack_slots * kInterpThreads * sizeof(float4) +
-                      (size_t)p.max_len * (sizeof(int) + sizeof(float));
+                      (size_t)p.max_len * sizeof(int2);
+  // feature offsets are 32-bit float4 indices
+  if (p.n_features <= 0 || (int64_t)p.n_features * (p.n_pad / 4) > (int64_t)INT32_MAX)
+    return cudaErrorInvalidValue;
   dim3 grid((unsigned)count, (unsigned)((p.n_pad + kInterpTile - 1) / kInterpTile));
   cudaError_t e = cudaSuccess;
   switch (mode) {
