@@ -164,16 +164,33 @@ class ClockSampler:
 def unique_bytes_per_generation(run, w: W.Workload, sigma_bytes: int):
     """Algorithmic DRAM bytes of each generation: every distinct parent row and
     every distinct random-tree row read once, every offspring row written
-    once, the targets read once (n_cases elements each)."""
+    once, the targets read once (n_cases elements each).  A crossover
+    offspring (rt2 = -2 - second parent) reads two parent rows and one
+    random-tree row."""
     par, r1, r2, _ = run.trace()
     n = w.n_cases
     out = []
     for g in range(par.shape[0]):
-        mut = r1[g] >= 0
-        u_p = len(np.unique(par[g][mut]))
-        u_r = len(np.unique(np.concatenate([r1[g][mut], r2[g][mut]])))
+        mut = (r1[g] >= 0) & (r2[g] >= 0)
+        cross = (r1[g] >= 0) & (r2[g] <= -2)
+        u_p = len(np.unique(np.concatenate([par[g][mut | cross], -2 - r2[g][cross]])))
+        u_r = len(np.unique(np.concatenate([r1[g][mut | cross], r2[g][mut]])))
         out.append((u_p + w.pop_size) * n * 4 + u_r * n * sigma_bytes + n * 4)
     return np.array(out, dtype=np.float64)
+
+
+def resolve_workload(args) -> W.Workload:
+    """The workload named on the command line with its overrides."""
+    w = W.WORKLOADS[args.workload]
+    if args.generations:
+        w = w.replace(generations=args.generations)
+    if args.pop_size:     # smaller pools of the same shape, e.g. for ncu captures
+        w = w.replace(pop_size=args.pop_size, n_random_trees=args.pop_size,
+                      name=f"{w.name.split(':')[0]} with m = r = {args.pop_size}")
+    if args.p_crossover > 0:
+        w = w.replace(p_crossover=args.p_crossover,
+                      name=f"{w.name} with crossover p = {args.p_crossover}")
+    return w
 
 
 def run_ours(args, rank, world, local_rank):
@@ -184,13 +201,7 @@ def run_ours(args, rank, world, local_rank):
 
     torch.cuda.set_device(local_rank)
     build_library()
-    w = W.WORKLOADS[args.workload]
-    if args.generations:
-        w = w.replace(generations=args.generations)
-    if args.pop_size:     # smaller pools of the same shape, e.g. for ncu captures
-        w = w.replace(pop_size=args.pop_size, n_random_trees=args.pop_size,
-                      name=f"{w.name.split(':')[0]} with m = r = {args.pop_size}")
-    w = replica_workload(w, rank)
+    w = replica_workload(resolve_workload(args), rank)
     G = w.generations
     data = W.make_data(w)
     Xtr, ytr, Xte, yte = data
@@ -350,7 +361,7 @@ def make_config(pkg, w: W.Workload, stream):
         tournament_size=w.tournament_size, const_lo=w.const_lo, const_hi=w.const_hi,
         protect_eps=w.protect_eps,
         sigma_dtype=pkg.SIGMA_BF16 if w.sigma_bf16 else pkg.SIGMA_F32,
-        init_mode=w.init_mode, max_genes=w.max_genes)
+        init_mode=w.init_mode, max_genes=w.max_genes, p_crossover=w.p_crossover)
     cfg.stream = stream.cuda_stream
     return cfg
 
@@ -517,14 +528,14 @@ def run_batched(args, rank, world, local_rank):
     return line, ws
 
 
-def cpu_baseline(w: W.Workload, target_s: float = 12.0, max_gens: int = 200):
-    """The float64 oracle, as it stands, on the host cores: generations of the
-    same workload until about target_s seconds of evolution were timed.  On
-    workloads whose initialisation would take the oracle many minutes the
-    sample keeps every case but at most 128 programs per pool."""
+def oracle_run(w: W.Workload):
+    """The float64 oracle initialised on workload w, or on a sample of it:
+    where the oracle's initialisation would take many minutes (long linear
+    genomes) every case is kept but at most 128 programs per pool.  Returns
+    (oracle, the workload it runs, a note on the sample)."""
     from oracle import gsgp as og
     full_m = w.pop_size
-    big = w.pop_size * w.n_cases * w.max_genes > 2e10 if w.init_mode == 1 else False
+    big = w.init_mode == 1 and w.pop_size * w.n_cases * w.max_genes > 2e10
     if big:
         w = w.replace(pop_size=min(w.pop_size, 128), n_random_trees=min(w.n_random_trees, 128))
     p = og.Params(seed=w.seed, run=w.run, pop_size=w.pop_size,
@@ -532,16 +543,25 @@ def cpu_baseline(w: W.Workload, target_s: float = 12.0, max_gens: int = 200):
                   pop_max_depth=w.pop_max_depth, rt_min_depth=w.rt_min_depth,
                   rt_max_depth=w.rt_max_depth, ms=w.ms, tournament_size=w.tournament_size,
                   const_lo=w.const_lo, const_hi=w.const_hi, protect_eps=w.protect_eps,
-                  sigma_bf16=w.sigma_bf16, init_mode=w.init_mode, max_genes=w.max_genes)
+                  sigma_bf16=w.sigma_bf16, init_mode=w.init_mode, max_genes=w.max_genes,
+                  p_crossover=w.p_crossover)
     o = og.GSGP(p, *W.make_data(w))
     o.init()
+    return o, w, (f", m and r cut from {full_m} to {w.pop_size}" if big else "")
+
+
+def cpu_baseline(w: W.Workload, target_s: float = 12.0, max_gens: int = 200):
+    """The float64 oracle, as it stands, on the host cores: generations of the
+    same workload until about target_s seconds of evolution were timed.  On
+    workloads whose initialisation would take the oracle many minutes the
+    sample keeps every case but at most 128 programs per pool."""
+    o, w, shrunk = oracle_run(w)
     t0 = time.perf_counter()
     gens = 0
     while gens < max_gens and (time.perf_counter() - t0) < target_s:
         o.generation()
         gens += 1
     dt = time.perf_counter() - t0
-    shrunk = f", m and r cut from {full_m} to {w.pop_size}" if big else ""
     return {"value": w.pop_size * w.n_cases * gens / dt, "unit": UNIT, "cores": 1,
             "kind": "oracle",
             "sample": f"{gens} generations of the {w.name.split(':')[0]} workload "
@@ -552,21 +572,11 @@ def cpu_baseline(w: W.Workload, target_s: float = 12.0, max_gens: int = 200):
 def run_reference(args, rank):
     """The CPU oracle as the reference arm: each step a bounded sample of the
     same workload (a few generations of the oracle after an untimed init)."""
-    from oracle import gsgp as og
     if args.workload == "batched":   # the smallest run of the batch
         w = min(W.batched_runs(args.batch_runs), key=lambda x: x.pop_size * x.n_cases)
     else:
-        w = W.WORKLOADS[args.workload]
-    if args.generations:
-        w = w.replace(generations=args.generations)
-    p = og.Params(seed=w.seed, run=w.run, pop_size=w.pop_size,
-                  n_random_trees=w.n_random_trees, pop_min_depth=w.pop_min_depth,
-                  pop_max_depth=w.pop_max_depth, rt_min_depth=w.rt_min_depth,
-                  rt_max_depth=w.rt_max_depth, ms=w.ms, tournament_size=w.tournament_size,
-                  const_lo=w.const_lo, const_hi=w.const_hi, protect_eps=w.protect_eps,
-                  sigma_bf16=w.sigma_bf16)
-    o = og.GSGP(p, *W.make_data(w))
-    o.init()
+        w = resolve_workload(args)
+    o, w, shrunk = oracle_run(w)
     gens_per_step = max(1, int(args.ref_gens_per_step))
     for _ in range(args.warmup):
         for _ in range(gens_per_step):
@@ -579,7 +589,8 @@ def run_reference(args, rank):
     gens = gens_per_step * args.steps
     value = w.pop_size * w.n_cases * gens / dt
     sample = (f"{gens_per_step} oracle generations per step of the {w.name.split(':')[0]} "
-              f"workload (full n_cases={w.n_cases}, m={w.pop_size}), float64 numpy, single thread")
+              f"workload (full n_cases={w.n_cases}, m={w.pop_size}{shrunk}), float64 numpy, "
+              f"single thread")
     return {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
@@ -605,6 +616,8 @@ def main():
     ap.add_argument("--ref-gens-per-step", type=int, default=3)
     ap.add_argument("--pop-size", type=int, default=0,
                     help="m = r override (smaller cases of a workload, e.g. for ncu captures)")
+    ap.add_argument("--p-crossover", type=float, default=0.0,
+                    help="probability of geometric semantic crossover (default 0)")
     ap.add_argument("--shape", default="",
                     help="vec,opb of the mutation stream instead of autotuning (e.g. 2,4)")
     ap.add_argument("--batch-runs", type=int, default=BATCH_RUNS,

@@ -51,6 +51,7 @@ class Workload:
     wid: int = 0                    # workload id, mixed into the data seed
     init_mode: int = 0              # 0 ramped half-and-half trees, 1 linear genomes
     max_genes: int = 127            # genome length (init_mode 1)
+    p_crossover: float = 0.0        # probability of geometric semantic crossover
 
     @property
     def n_cases(self) -> int:
