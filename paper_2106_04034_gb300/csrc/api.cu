@@ -2,6 +2,7 @@
 // ordering, CUDA-graph replay of the generation loop and host-side model
 // reconstruction.  Every step of the method runs in the kernels of
 // k_init.cu, k_generation.cu and k_predict.cu.
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstddef>
@@ -10,6 +11,7 @@
 #include <new>
 #include <string>
 #include <unordered_map>
+#include <utility>
 #include <vector>
 
 #include "ctx.h"
@@ -1195,38 +1197,98 @@ static gsgp_status run_predict(gsgp_ctx *c, const float *X_dev_rows, int64_t n, 
   return GSGP_OK;
 }
 
-// Runs with crossover: replay every generation on the new cases (float64).
+// Runs with crossover: replay the generations on the new cases (float64).
+// Only the ancestors of the best slot are replayed: a backward pass over the
+// trace (host) lists, for every generation, the slots whose values a later
+// listed slot reads (one parent for a mutation or copy, two for a
+// crossover); under tournament selection that is about a quarter of the
+// population, and a handful of slots in the last generations.
 static gsgp_status run_predict_replay(gsgp_ctx *c, const float *X_dev_rows, int64_t n,
                                       double *y_dev) {
-  const int m = c->cfg.pop_size, r = c->cfg.n_random_trees;
+  const int m = c->cfg.pop_size, r = c->cfg.n_random_trees, G = c->gen;
   const int64_t n_pad = (n + 3) / 4 * 4;
-  float *Xt = nullptr;
-  double *S0 = nullptr, *S1 = nullptr, *Sr = nullptr;
-  TRY(dalloc_n(c, &Xt, (size_t)c->l * n_pad));
-  TRY(dalloc_n(c, &S0, (size_t)m * n_pad));
-  TRY(dalloc_n(c, &S1, (size_t)m * n_pad));
-  TRY(dalloc_n(c, &Sr, (size_t)r * n_pad));
-  LAUNCH(1, launch_transpose(X_dev_rows, n, c->l, Xt, n_pad, 0, c->stream));
-  LAUNCH(1, launch_eval_pool(prog_genes(c, true), prog_consts(c, true), prog_len(c, true), c->Kp,
-                             m, Xt, n_pad, n, S0, c->cfg.protect_eps, 0, c->stream));
-  LAUNCH(1, launch_eval_pool(prog_genes(c, false), prog_consts(c, false), prog_len(c, false),
-                             c->Kr, r, Xt, n_pad, n, Sr, c->cfg.protect_eps,
-                             c->cfg.sigma_dtype == GSGP_SIGMA_BF16 ? 2 : 1, c->stream));
-  for (int g = 0; g < c->gen; ++g) {
-    LAUNCH(1, launch_replay(c->trace + (size_t)g * m, m, S0, S1, Sr, n_pad, n, c->stream));
-    double *t = S0;
-    S0 = S1;
-    S1 = t;
-  }
+  struct Bufs {
+    gsgp_ctx *c;
+    float *Xt = nullptr;
+    double *S0 = nullptr, *S1 = nullptr, *Sr = nullptr;
+    int *slots = nullptr, *off = nullptr;
+    ~Bufs() {
+      dfree(c, Xt);
+      dfree(c, S0);
+      dfree(c, S1);
+      dfree(c, Sr);
+      dfree(c, slots);
+      dfree(c, off);
+    }
+  } b{c};
   DevState st{};
+  std::vector<int4> tr((size_t)G * m);
   CK(cudaMemcpyAsync(&st, c->dstate, sizeof st, cudaMemcpyDeviceToHost, c->stream));
+  if (G > 0)
+    CK(cudaMemcpyAsync(tr.data(), c->trace, sizeof(int4) * tr.size(), cudaMemcpyDeviceToHost,
+                       c->stream));
   CK(cudaStreamSynchronize(c->stream));
-  CK(cudaMemcpyAsync(y_dev, S0 + (size_t)st.best_slot * n_pad, sizeof(double) * (size_t)n,
-                     cudaMemcpyDeviceToDevice, c->stream));
-  dfree(c, Xt);
-  dfree(c, S0);
-  dfree(c, S1);
-  dfree(c, Sr);
+  if (st.best_slot < 0 || st.best_slot >= m) return fail(c, GSGP_E_STATE, "no best slot");
+  // backward: need[i] = slot i's value at generation g is read later
+  std::vector<std::vector<int>> lists((size_t)G);
+  std::vector<char> need((size_t)m, 0), prev((size_t)m);
+  need[(size_t)st.best_slot] = 1;
+  for (int g = G - 1; g >= 0; --g) {
+    std::fill(prev.begin(), prev.end(), 0);
+    std::vector<int> &lg = lists[(size_t)g];
+    for (int i = 0; i < m; ++i) {
+      if (!need[(size_t)i]) continue;
+      lg.push_back(i);
+      const int4 e = tr[(size_t)g * m + i];
+      const int p2 = (e.y >= 0 && e.z <= -2) ? -2 - e.z : -1;
+      if (e.x < 0 || e.x >= m || (e.y >= r) || (e.y >= 0 && p2 < 0 && (e.z < 0 || e.z >= r)) ||
+          p2 >= m)
+        return fail(c, GSGP_E_STATE, "corrupt trace entry at generation %d, slot %d", g, i);
+      prev[(size_t)e.x] = 1;
+      if (p2 >= 0) prev[(size_t)p2] = 1;
+    }
+    need.swap(prev);
+  }
+  std::vector<int> flat, off((size_t)G + 1, 0);
+  for (int g = 0; g < G; ++g) {
+    flat.insert(flat.end(), lists[(size_t)g].begin(), lists[(size_t)g].end());
+    off[(size_t)g + 1] = (int)flat.size();
+  }
+  TRY(dalloc_n(c, &b.Xt, (size_t)c->l * n_pad));
+  TRY(dalloc_n(c, &b.S0, (size_t)m * n_pad));
+  TRY(dalloc_n(c, &b.Sr, (size_t)r * n_pad));
+  TRY(dalloc_n(c, &b.slots, flat.size() ? flat.size() : 1));
+  TRY(dalloc_n(c, &b.off, off.size()));
+  if (!flat.empty())
+    CK(cudaMemcpyAsync(b.slots, flat.data(), sizeof(int) * flat.size(), cudaMemcpyHostToDevice,
+                       c->stream));
+  CK(cudaMemcpyAsync(b.off, off.data(), sizeof(int) * off.size(), cudaMemcpyHostToDevice,
+                     c->stream));
+  LAUNCH(1, launch_transpose(X_dev_rows, n, c->l, b.Xt, n_pad, 0, c->stream));
+  LAUNCH(1, launch_eval_pool(prog_genes(c, true), prog_consts(c, true), prog_len(c, true), c->Kp,
+                             m, b.Xt, n_pad, n, b.S0, c->cfg.protect_eps, 0, c->stream));
+  LAUNCH(1, launch_eval_pool(prog_genes(c, false), prog_consts(c, false), prog_len(c, false),
+                             c->Kr, r, b.Xt, n_pad, n, b.Sr, c->cfg.protect_eps,
+                             c->cfg.sigma_dtype == GSGP_SIGMA_BF16 ? 2 : 1, c->stream));
+  // one case per CTA measured fastest (more CTAs resident per SM; 2-8 cases
+  // per CTA were 1-4% slower on 1024-slot pools)
+  const int lt = replay_tile_log2(m, r) >= 0 ? 0 : -1;
+  if (lt >= 0) {   // every generation in one launch, the values in shared memory
+    LAUNCH(1, launch_replay_tiles(c->trace, b.slots, b.off, G, m, r, b.S0, b.Sr, n_pad, n,
+                                  st.best_slot, y_dev, lt, c->stream));
+  } else {   // pools too large for shared memory: one launch per generation
+    TRY(dalloc_n(c, &b.S1, (size_t)m * n_pad));
+    double *cur = b.S0, *nxt = b.S1;
+    for (int g = 0; g < G; ++g) {
+      LAUNCH(1, launch_replay(c->trace + (size_t)g * m, b.slots + off[(size_t)g],
+                              off[(size_t)g + 1] - off[(size_t)g], cur, nxt, b.Sr, n_pad, n,
+                              c->stream));
+      std::swap(cur, nxt);
+    }
+    CK(cudaMemcpyAsync(y_dev, cur + (size_t)st.best_slot * n_pad, sizeof(double) * (size_t)n,
+                       cudaMemcpyDeviceToDevice, c->stream));
+  }
+  CK(cudaStreamSynchronize(c->stream));   // the host lists above are read by the copies
   return GSGP_OK;
 }
 

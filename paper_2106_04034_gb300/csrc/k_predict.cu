@@ -189,60 +189,150 @@ __global__ void __launch_bounds__(kPredWarps * 32) predict_kernel(const PredictP
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(128)
     eval_pool_kernel(const int *__restrict__ genes, const float *__restrict__ consts,
-                     const int *__restrict__ lengths, int K, const float *__restrict__ X,
-                     int64_t n_pad, int64_t n, double *__restrict__ out, float eps, int mode) {
+                     const int *__restrict__ lengths, int K, int count,
+                     const float *__restrict__ X, int64_t n_pad, int64_t n,
+                     double *__restrict__ out, float eps, int mode) {
   const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int prog = blockIdx.y;
   if (j >= n) return;
-  const int *g = genes + (size_t)prog * K;
-  const float *c = consts + (size_t)prog * K;
-  double v;
-  if (mode == 2) {   // the training's bf16 sigma
-    const float f = eval_program32(g, c, lengths[prog], X, n_pad, j, eps);
-    v = (double)__bfloat162float(__float2bfloat16_rn(1.0f / (1.0f + expf(-f))));
-  } else {
-    v = eval_program64(g, c, lengths[prog], X, n_pad, j, (double)eps);
-    if (mode == 1) v = 1.0 / (1.0 + exp(-v));
+  for (int prog = blockIdx.y; prog < count; prog += gridDim.y) {
+    const int *g = genes + (size_t)prog * K;
+    const float *c = consts + (size_t)prog * K;
+    double v;
+    if (mode == 2) {   // the training's bf16 sigma
+      const float f = eval_program32(g, c, lengths[prog], X, n_pad, j, eps);
+      v = (double)__bfloat162float(__float2bfloat16_rn(1.0f / (1.0f + expf(-f))));
+    } else {
+      v = eval_program64(g, c, lengths[prog], X, n_pad, j, (double)eps);
+      if (mode == 1) v = 1.0 / (1.0 + exp(-v));
+    }
+    out[(size_t)prog * n_pad + j] = v;
   }
-  out[(size_t)prog * n_pad + j] = v;
 }
 
 __global__ void __launch_bounds__(128)
-    replay_kernel(const int4 *__restrict__ entries, const double *__restrict__ prev,
-                  double *__restrict__ next, const double *__restrict__ sig, int64_t n_pad,
-                  int64_t n) {
+    replay_kernel(const int4 *__restrict__ entries, const int *__restrict__ slots, int count,
+                  const double *__restrict__ prev, double *__restrict__ next,
+                  const double *__restrict__ sig, int64_t n_pad, int64_t n) {
   const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int i = blockIdx.y;
   if (j >= n) return;
-  const int4 e = entries[i];
-  const double t1 = prev[(size_t)e.x * n_pad + j];
-  double v;
-  if (e.y < 0) {
-    v = t1;
-  } else if (e.z <= -2) {
-    const double rm = sig[(size_t)e.y * n_pad + j];
-    v = rm * t1 + (1.0 - rm) * prev[(size_t)(-2 - e.z) * n_pad + j];
-  } else {
-    const double ms = (double)__int_as_float(e.w);
-    v = t1 + ms * (sig[(size_t)e.y * n_pad + j] - sig[(size_t)e.z * n_pad + j]);
+  for (int k = blockIdx.y; k < count; k += gridDim.y) {
+    const int i = slots[k];
+    const int4 e = entries[i];
+    const double t1 = prev[(size_t)e.x * n_pad + j];
+    double v;
+    if (e.y < 0) {
+      v = t1;
+    } else if (e.z <= -2) {
+      const double rm = sig[(size_t)e.y * n_pad + j];
+      v = __fma_rn(rm, t1, (1.0 - rm) * prev[(size_t)(-2 - e.z) * n_pad + j]);
+    } else {
+      const double ms = (double)__int_as_float(e.w);
+      v = __fma_rn(ms, sig[(size_t)e.y * n_pad + j] - sig[(size_t)e.z * n_pad + j], t1);
+    }
+    next[(size_t)i * n_pad + j] = v;
   }
-  next[(size_t)i * n_pad + j] = v;
+}
+
+// The whole replay for a tile of 2^lt consecutive new cases in one CTA: the
+// population's values ([slot][case], two buffers that alternate by
+// generation) and the random trees' values of the tile stay in shared
+// memory for all G generations; the slot lists and trace entries come from
+// L2, where every CTA reads the same ones.  Generation g computes only the
+// slots slots[off[g] .. off[g + 1]), the ancestors of the final slot `best`
+// (a slot left out keeps a stale value that no later listed slot reads).
+// The arithmetic is replay_kernel's, so both give the same bits.
+__global__ void __launch_bounds__(256)
+    replay_tile_kernel(const int4 *__restrict__ entries, const int *__restrict__ slots,
+                       const int *__restrict__ off, int G, int m, int r,
+                       const double *__restrict__ S0, const double *__restrict__ Sr,
+                       int64_t n_pad, int64_t n, int best, double *__restrict__ y, int lt) {
+  extern __shared__ double s_val[];
+  const int T = 1 << lt, tm = T - 1;
+  double *cur = s_val, *nxt = s_val + (size_t)m * T;
+  double *sig = s_val + (size_t)2 * m * T;
+  const int64_t j0 = (int64_t)blockIdx.x * T;
+  const int tc = (int)(n - j0 < T ? n - j0 : T);   // cases of this tile
+  for (int e = threadIdx.x; e < m * T; e += blockDim.x) {
+    const int q = e & tm;
+    cur[e] = q < tc ? S0[(size_t)(e >> lt) * n_pad + j0 + q] : 0.0;
+  }
+  for (int e = threadIdx.x; e < r * T; e += blockDim.x) {
+    const int q = e & tm;
+    sig[e] = q < tc ? Sr[(size_t)(e >> lt) * n_pad + j0 + q] : 0.0;
+  }
+  __syncthreads();
+  for (int g = 0; g < G; ++g) {
+    const int4 *eg = entries + (size_t)g * m;
+    const int *lg = slots + __ldg(off + g);
+    const int cnt = __ldg(off + g + 1) - __ldg(off + g);
+    for (int e = threadIdx.x; e < (cnt << lt); e += blockDim.x) {
+      const int q = e & tm;
+      const int i = __ldg(lg + (e >> lt));
+      const int4 en = __ldg(eg + i);
+      const double t1 = cur[(en.x << lt) + q];
+      double v;
+      if (en.y < 0) {
+        v = t1;
+      } else if (en.z <= -2) {
+        const double rm = sig[(en.y << lt) + q];
+        v = __fma_rn(rm, t1, (1.0 - rm) * cur[((-2 - en.z) << lt) + q]);
+      } else {
+        const double ms = (double)__int_as_float(en.w);
+        v = __fma_rn(ms, sig[(en.y << lt) + q] - sig[(en.z << lt) + q], t1);
+      }
+      nxt[(i << lt) + q] = v;
+    }
+    __syncthreads();
+    double *t = cur;
+    cur = nxt;
+    nxt = t;
+  }
+  for (int q = threadIdx.x; q < tc; q += blockDim.x) y[j0 + q] = cur[(best << lt) + q];
+}
+
+int replay_tile_log2(int m, int r) {
+  int dev = 0, smem = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+    return -1;
+  const size_t per_case = (size_t)(2 * m + r) * sizeof(double);
+  int lt = -1;
+  while (lt < 5 && per_case << (lt + 1) <= (size_t)smem) ++lt;
+  return lt;   // -1: not even one case fits
+}
+
+cudaError_t launch_replay_tiles(const int4 *entries, const int *slots, const int *off, int G,
+                                int m, int r, const double *S0, const double *Sr, int64_t n_pad,
+                                int64_t n, int best, double *y, int lt, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  if (lt < 0 || lt > 5) return cudaErrorInvalidValue;
+  const size_t smem = ((size_t)(2 * m + r) * sizeof(double)) << lt;
+  cudaError_t e = cudaFuncSetAttribute(replay_tile_kernel,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const int64_t tiles = (n + (1 << lt) - 1) >> lt;
+  replay_tile_kernel<<<(unsigned)tiles, 256, smem, s>>>(entries, slots, off, G, m, r, S0, Sr,
+                                                        n_pad, n, best, y, lt);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_eval_pool(const int *genes, const float *consts, const int *lengths, int K,
                              int count, const float *X, int64_t n_pad, int64_t n, double *out,
                              float eps, int mode, cudaStream_t s) {
   if (count <= 0 || n <= 0) return cudaSuccess;
-  eval_pool_kernel<<<dim3((unsigned)((n + 127) / 128), (unsigned)count), 128, 0, s>>>(
-      genes, consts, lengths, K, X, n_pad, n, out, eps, mode);
+  const unsigned gy = (unsigned)(count < 65535 ? count : 65535);
+  eval_pool_kernel<<<dim3((unsigned)((n + 127) / 128), gy), 128, 0, s>>>(
+      genes, consts, lengths, K, count, X, n_pad, n, out, eps, mode);
   return cudaGetLastError();
 }
 
-cudaError_t launch_replay(const int4 *entries, int m, const double *prev, double *next,
-                          const double *sig, int64_t n_pad, int64_t n, cudaStream_t s) {
-  if (m <= 0 || n <= 0) return cudaSuccess;
-  replay_kernel<<<dim3((unsigned)((n + 127) / 128), (unsigned)m), 128, 0, s>>>(entries, prev, next,
-                                                                            sig, n_pad, n);
+cudaError_t launch_replay(const int4 *entries, const int *slots, int count, const double *prev,
+                          double *next, const double *sig, int64_t n_pad, int64_t n,
+                          cudaStream_t s) {
+  if (count <= 0 || n <= 0) return cudaSuccess;
+  const unsigned gy = (unsigned)(count < 65535 ? count : 65535);
+  replay_kernel<<<dim3((unsigned)((n + 127) / 128), gy), 128, 0, s>>>(entries, slots, count, prev,
+                                                                     next, sig, n_pad, n);
   return cudaGetLastError();
 }
 

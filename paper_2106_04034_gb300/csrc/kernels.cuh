@@ -142,8 +142,17 @@ cudaError_t launch_predict(const PredictParams &p, cudaStream_t s);
 cudaError_t launch_eval_pool(const int *genes, const float *consts, const int *lengths, int K,
                              int count, const float *X, int64_t n_pad, int64_t n, double *out,
                              float eps, int mode, cudaStream_t s);
-cudaError_t launch_replay(const int4 *entries, int m, const double *prev, double *next,
-                          const double *sig, int64_t n_pad, int64_t n, cudaStream_t s);
+// One generation's entries applied to the slots slots[0 .. count).
+cudaError_t launch_replay(const int4 *entries, const int *slots, int count, const double *prev,
+                          double *next, const double *sig, int64_t n_pad, int64_t n,
+                          cudaStream_t s);
+// All G generations in one launch, 2^lt cases per CTA held in shared memory,
+// generation g computing slots[off[g] .. off[g + 1]); replay_tile_log2 gives
+// the largest lt (at most 5) that fits, or -1.
+int replay_tile_log2(int m, int r);
+cudaError_t launch_replay_tiles(const int4 *entries, const int *slots, const int *off, int G,
+                                int m, int r, const double *S0, const double *Sr, int64_t n_pad,
+                                int64_t n, int best, double *y, int lt, cudaStream_t s);
 
 cudaError_t launch_rng_words(uint2 key, uint32_t run, uint32_t gp, uint32_t individual,
                              int n_words, uint32_t *out, cudaStream_t s);

@@ -141,3 +141,19 @@ def test_checkpoint_resumes_a_run_with_crossover():
         c.restore(ck)
     for r in (straight, a, b, c):
         r.close()
+
+
+def test_prediction_of_pools_too_large_for_shared_memory():
+    # 2m + r float64 values per case no longer fit one CTA's shared memory:
+    # prediction takes one replay launch per generation instead of the tiles
+    w = XO.replace(pop_size=10240, n_random_trees=10240)
+    run, data, p = gpu_run(w, p_crossover=0.5)
+    run.evolve(6, log=False)
+    ref = og.GSGP(p, *data)
+    ref.create_programs()
+    Xn = W.make_new_cases(w, 300)
+    got = run.predict(Xn)
+    want = og.predict_replay(run.trace(), _best(run), ref.P, ref.R, og.feature_major(Xn),
+                             p.protect_eps)
+    assert np.allclose(got, want, rtol=1e-9, atol=1e-9)
+    run.close()
