@@ -88,3 +88,37 @@ def replay(ref: og.GSGP, trace, G0=0):
 
 def hard_failures(checks):
     return {k: v for k, v in checks.items() if not k.endswith("near_tie")}
+
+
+def f32_program(genes, consts, X, eps):
+    """Float32 value of one program on the cases X (features, n): a stack
+    machine with the skip rule and the Out register."""
+    n = X.shape[1]
+    stack, out = [], None
+    with np.errstate(all="ignore"):
+        for g, c in zip(genes, consts):
+            g = int(g)
+            if g == -1:
+                break
+            op = g & 0xFF
+            if op == 5:
+                stack.append(X[g >> 8])
+            elif op == 4:
+                stack.append(np.full(n, c, np.float32))
+            elif len(stack) >= 2:
+                b = stack.pop()
+                a = stack.pop()
+                if op == 0:
+                    r = a + b
+                elif op == 1:
+                    r = a - b
+                elif op == 2:
+                    r = a * b
+                else:
+                    r = np.where(np.abs(b) < eps, np.float32(1), a / b)
+                r = r.astype(np.float32)
+                stack.append(r)
+                out = r
+    if out is not None:
+        return out
+    return stack[-1] if stack else np.zeros(n, np.float32)
