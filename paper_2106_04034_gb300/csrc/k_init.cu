@@ -441,6 +441,11 @@ __device__ __forceinline__ float4 apply4(int f, const float4 a, const float4 b, 
   }
 }
 
+template <int F>
+__device__ __forceinline__ float4 op4(const float4 a, const float4 b, float eps) {
+  return apply4(F, a, b, eps);
+}
+
 // Decoded gene of the interpreter's loop: bits 0-1 the function, bit 2 a
 // terminal operand (alone or fused), bit 3 the terminal is a feature, bit 4
 // a function (alone or fused); the argument is the feature row's offset in
@@ -477,26 +482,53 @@ __global__ void __launch_bounds__(kInterpThreads) interpret_kernel(InterpParams 
   float4 *stk = s_stack + tid;   // this thread's column of the stack
   float4 tos = make_float4(0.f, 0.f, 0.f, 0.f);
   int sp = 0;
+  // one jump per gene: every (kind, operator) pair has its own straight-line case
+  auto push = [&](const float4 v) {
+    if (sp > 0 && sp - 1 < p.stack_slots) stk[(sp - 1) * kInterpThreads] = tos;
+    tos = v;
+    ++sp;
+  };
+  const float eps = p.protect_eps;
   for (int k = 0; k < len; ++k) {
     const int2 e = s_prog[k];
-    if (e.x & kDecTerm) {   // a terminal, alone or fused with the function after it
-      float4 v;
-      if (e.x & kDecVar) {
-        v = __ldg(xcase + e.y);
-      } else {
-        const float c = __int_as_float(e.y);
-        v = make_float4(c, c, c, c);
-      }
-      if ((e.x & kDecFun) && sp >= 1) {   // f(stack top, terminal), no push or pop
-        tos = apply4(e.x & 3, tos, v, p.protect_eps);
-      } else {
-        if (sp > 0 && sp - 1 < p.stack_slots) stk[(sp - 1) * kInterpThreads] = tos;
-        tos = v;
-        ++sp;
-      }
-    } else if (sp >= 2) {
-      tos = apply4(e.x & 3, stk[(sp - 2) * kInterpThreads], tos, p.protect_eps);
-      --sp;
+    const float cf = __int_as_float(e.y);
+    switch (e.x) {
+#define GSGP_FUN(F)                                                                      \
+  case kDecFun | F:                                                                      \
+    if (sp >= 2) {                                                                       \
+      tos = op4<F>(stk[(sp - 2) * kInterpThreads], tos, eps);                            \
+      --sp;                                                                              \
+    }                                                                                    \
+    break;                                                                               \
+  case kDecTerm | kDecFun | F: {                                                         \
+    const float4 v = make_float4(cf, cf, cf, cf);                                        \
+    if (sp >= 1)                                                                         \
+      tos = op4<F>(tos, v, eps);                                                         \
+    else                                                                                 \
+      push(v);                                                                           \
+    break;                                                                               \
+  }                                                                                      \
+  case kDecTerm | kDecVar | kDecFun | F: {                                               \
+    const float4 v = __ldg(xcase + e.y);                                                 \
+    if (sp >= 1)                                                                         \
+      tos = op4<F>(tos, v, eps);                                                         \
+    else                                                                                 \
+      push(v);                                                                           \
+    break;                                                                               \
+  }
+      GSGP_FUN(kOpAdd)
+      GSGP_FUN(kOpSub)
+      GSGP_FUN(kOpMul)
+      GSGP_FUN(kOpDiv)
+#undef GSGP_FUN
+      case kDecTerm:
+        push(make_float4(cf, cf, cf, cf));
+        break;
+      case kDecTerm | kDecVar:
+        push(__ldg(xcase + e.y));
+        break;
+      default:
+        break;
     }
   }
   // The program's value is register Out (Sec. 2.2, "Interpreter"): every
