@@ -284,7 +284,8 @@ def run_ours(args, rank, world, local_rank):
     # the interpreter (ComputeSemantics of P and R): one gene applied to one
     # case is the unit of work, one lane operation at the least, against the
     # FP32 lanes' issue rate (152 SMs x 128 lanes x clock)
-    # (the evaluated genes: for linear genomes the live code, see DESIGN)
+    # (the evaluated genes: for linear genomes the live code, the expression
+    # under register Out; generated trees are evaluated whole)
     info_i = run.info()
     gene_cases = float(info_i.pop_evaluated_genes + info_i.rt_evaluated_genes) * w.n_cases
     genome_cases = float(sum(run.programs(pool)[2].sum()
