@@ -94,8 +94,9 @@ enum { GSGP_INIT_RHH = 0, GSGP_INIT_LINEAR = 1 };
  * T2 + R (T1 - T2) in float32.  Its trace entry is (parent 1, mask tree,
  * -2 - parent 2, 0).  Runs with crossover have no ancestor-plus-coefficients
  * model (gsgp_best_trace returns GSGP_E_STATE); gsgp_predict then replays
- * the trace on the new cases in float64.  The TMA-staged stream shapes do
- * not support crossover. */
+ * the trace on the new cases in float64, for the ancestors of the best slot
+ * only (the trace is copied to the host once per call to list them).  The
+ * TMA-staged stream shapes do not support crossover. */
 enum { GSGP_POOL_POPULATION = 0, GSGP_POOL_RANDOM = 1 };
 
 /* Optional device allocator.  alloc returns device memory of at least
