@@ -460,12 +460,31 @@ __device__ __forceinline__ int2 decode_gene(int g, float c, int64_t row4) {
   return make_int2(code, var ? (int)((g >> 8) * row4) : __float_as_int(c));
 }
 
-template <int MODE>
+// The values of one stack entry for the thread's VEC chunks (4 cases each).
+template <int VEC>
+struct Lanes {
+  float4 v[VEC];
+};
+
+template <int F, int VEC>
+__device__ __forceinline__ Lanes<VEC> opv(const Lanes<VEC> &a, const Lanes<VEC> &b, float eps) {
+  Lanes<VEC> r;
+#pragma unroll
+  for (int q = 0; q < VEC; ++q) r.v[q] = op4<F>(a.v[q], b.v[q], eps);
+  return r;
+}
+
+// A CTA interprets one program over VEC chunks of 1024 cases: thread t holds
+// cases 4t .. 4t + 3 of each chunk, so one decoded gene serves 4 VEC cases.
+// The stack below the top lives in shared memory as [slot][chunk][thread];
+// each chunk's squared errors are reduced exactly as with one chunk per CTA.
+template <int MODE, int VEC>
 __global__ void __launch_bounds__(kInterpThreads) interpret_kernel(InterpParams p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float4 *s_stack = reinterpret_cast<float4 *>(smem_raw);
-  int2 *s_prog = reinterpret_cast<int2 *>(s_stack + (size_t)p.stack_slots * kInterpThreads);
-  __shared__ float2 s_sub[kInterpThreads / 32];   // sub-block (warp) totals
+  int2 *s_prog =
+      reinterpret_cast<int2 *>(s_stack + (size_t)p.stack_slots * VEC * kInterpThreads);
+  __shared__ float2 s_sub[VEC][kInterpThreads / 32];   // sub-block (warp) totals per chunk
 
   const int prog = p.order ? p.order[blockIdx.x] : (int)blockIdx.x;
   const int tile = blockIdx.y;
@@ -476,42 +495,70 @@ __global__ void __launch_bounds__(kInterpThreads) interpret_kernel(InterpParams 
     s_prog[k] = decode_gene(p.genes[(size_t)prog * p.K + k], p.consts[(size_t)prog * p.K + k], row4);
   __syncthreads();
 
-  const int64_t j4 = (int64_t)tile * kInterpThreads + tid;   // float4 index
-  const bool valid = j4 * 4 < p.n_pad;
-  const float4 *xcase = reinterpret_cast<const float4 *>(p.X) + (valid ? j4 : 0);
-  float4 *stk = s_stack + tid;   // this thread's column of the stack
-  float4 tos = make_float4(0.f, 0.f, 0.f, 0.f);
+  int64_t j4[VEC];   // float4 index of the thread's cases in chunk q
+  bool valid[VEC];
+  const float4 *xcase[VEC];
+#pragma unroll
+  for (int q = 0; q < VEC; ++q) {
+    j4[q] = ((int64_t)tile * VEC + q) * kInterpThreads + tid;
+    valid[q] = j4[q] * 4 < p.n_pad;
+    xcase[q] = reinterpret_cast<const float4 *>(p.X) + (valid[q] ? j4[q] : 0);
+  }
+  float4 *stk = s_stack + tid;   // entry s, chunk q at stk[(s * VEC + q) * kInterpThreads]
+  Lanes<VEC> tos;
+#pragma unroll
+  for (int q = 0; q < VEC; ++q) tos.v[q] = make_float4(0.f, 0.f, 0.f, 0.f);
   int sp = 0;
-  // one jump per gene: every (kind, operator) pair has its own straight-line case
-  auto push = [&](const float4 v) {
-    if (sp > 0 && sp - 1 < p.stack_slots) stk[(sp - 1) * kInterpThreads] = tos;
-    tos = v;
+  auto push = [&](const Lanes<VEC> &x) {
+    if (sp > 0 && sp - 1 < p.stack_slots) {
+#pragma unroll
+      for (int q = 0; q < VEC; ++q) stk[((sp - 1) * VEC + q) * kInterpThreads] = tos.v[q];
+    }
+    tos = x;
     ++sp;
   };
+  auto below = [&]() {   // the entry under the top
+    Lanes<VEC> a;
+#pragma unroll
+    for (int q = 0; q < VEC; ++q) a.v[q] = stk[((sp - 2) * VEC + q) * kInterpThreads];
+    return a;
+  };
+  auto feature = [&](int off) {
+    Lanes<VEC> a;
+#pragma unroll
+    for (int q = 0; q < VEC; ++q) a.v[q] = __ldg(xcase[q] + off);
+    return a;
+  };
+  auto constant = [&](float c) {
+    Lanes<VEC> a;
+#pragma unroll
+    for (int q = 0; q < VEC; ++q) a.v[q] = make_float4(c, c, c, c);
+    return a;
+  };
   const float eps = p.protect_eps;
+  // one jump per gene: every (kind, operator) pair has its own straight-line case
   for (int k = 0; k < len; ++k) {
     const int2 e = s_prog[k];
-    const float cf = __int_as_float(e.y);
     switch (e.x) {
 #define GSGP_FUN(F)                                                                      \
   case kDecFun | F:                                                                      \
     if (sp >= 2) {                                                                       \
-      tos = op4<F>(stk[(sp - 2) * kInterpThreads], tos, eps);                            \
+      tos = opv<F, VEC>(below(), tos, eps);                                              \
       --sp;                                                                              \
     }                                                                                    \
     break;                                                                               \
   case kDecTerm | kDecFun | F: {                                                         \
-    const float4 v = make_float4(cf, cf, cf, cf);                                        \
+    const Lanes<VEC> v = constant(__int_as_float(e.y));                                  \
     if (sp >= 1)                                                                         \
-      tos = op4<F>(tos, v, eps);                                                         \
+      tos = opv<F, VEC>(tos, v, eps);                                                    \
     else                                                                                 \
       push(v);                                                                           \
     break;                                                                               \
   }                                                                                      \
   case kDecTerm | kDecVar | kDecFun | F: {                                               \
-    const float4 v = __ldg(xcase + e.y);                                                 \
+    const Lanes<VEC> v = feature(e.y);                                                   \
     if (sp >= 1)                                                                         \
-      tos = op4<F>(tos, v, eps);                                                         \
+      tos = opv<F, VEC>(tos, v, eps);                                                    \
     else                                                                                 \
       push(v);                                                                           \
     break;                                                                               \
@@ -522,10 +569,10 @@ __global__ void __launch_bounds__(kInterpThreads) interpret_kernel(InterpParams 
       GSGP_FUN(kOpDiv)
 #undef GSGP_FUN
       case kDecTerm:
-        push(make_float4(cf, cf, cf, cf));
+        push(constant(__int_as_float(e.y)));
         break;
       case kDecTerm | kDecVar:
-        push(__ldg(xcase + e.y));
+        push(feature(e.y));
         break;
       default:
         break;
@@ -537,71 +584,81 @@ __global__ void __launch_bounds__(kInterpThreads) interpret_kernel(InterpParams 
   // function applied), so Out is the final stack top; an empty program is 0.
 
   if (MODE == 0) {
-    float str = 0.f, ste = 0.f;
-    if (valid) {
-      reinterpret_cast<float4 *>(static_cast<float *>(p.out) + (int64_t)prog * p.n_pad)[j4] = tos;
-      const float4 t = __ldg(reinterpret_cast<const float4 *>(p.target) + j4);
-      const float v[4] = {tos.x, tos.y, tos.z, tos.w};
-      const float tt[4] = {t.x, t.y, t.z, t.w};
+    const int lane = tid & 31, warp = tid >> 5;
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int64_t j = j4 * 4 + q;
-        const float d = v[q] - tt[q];
-        if (j < p.n_train)
-          str += d * d;
-        else if (j < p.n_cases)
-          ste += d * d;
+    for (int q = 0; q < VEC; ++q) {
+      float str = 0.f, ste = 0.f;
+      if (valid[q]) {
+        reinterpret_cast<float4 *>(static_cast<float *>(p.out) + (int64_t)prog * p.n_pad)[j4[q]] =
+            tos.v[q];
+        const float4 t = __ldg(reinterpret_cast<const float4 *>(p.target) + j4[q]);
+        const float vv[4] = {tos.v[q].x, tos.v[q].y, tos.v[q].z, tos.v[q].w};
+        const float tt[4] = {t.x, t.y, t.z, t.w};
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          const int64_t j = j4[q] * 4 + c;
+          const float d = vv[c] - tt[c];
+          if (j < p.n_train)
+            str += d * d;
+          else if (j < p.n_cases)
+            ste += d * d;
+        }
       }
+      const float2 sub = subblock_sum(str, ste);
+      if (lane == 0) s_sub[q][warp] = sub;
     }
-    const float2 sub = subblock_sum(str, ste);
-    if ((tid & 31) == 0) s_sub[tid >> 5] = sub;
     __syncthreads();
-    if (tid == 0) p.partial[(size_t)prog * p.tiles + tile] = chunk_total(s_sub);
-  } else if (valid) {
-    const float4 sg = make_float4(logistic(tos.x), logistic(tos.y), logistic(tos.z),
-                                  logistic(tos.w));
-    if (MODE == 1) {
-      reinterpret_cast<float4 *>(static_cast<float *>(p.out) + (int64_t)prog * p.n_pad)[j4] = sg;
-    } else {
-      __nv_bfloat162 lo = __floats2bfloat162_rn(sg.x, sg.y);
-      __nv_bfloat162 hi = __floats2bfloat162_rn(sg.z, sg.w);
-      uint2 packed;
-      packed.x = *reinterpret_cast<uint32_t *>(&lo);
-      packed.y = *reinterpret_cast<uint32_t *>(&hi);
-      reinterpret_cast<uint2 *>(static_cast<__nv_bfloat16 *>(p.out) + (int64_t)prog * p.n_pad)[j4] =
-          packed;
+    if (tid < VEC && tile * VEC + tid < p.tiles)
+      p.partial[(size_t)prog * p.tiles + tile * VEC + tid] = chunk_total(s_sub[tid]);
+  } else {
+#pragma unroll
+    for (int q = 0; q < VEC; ++q) {
+      if (!valid[q]) continue;
+      const float4 t4 = tos.v[q];
+      const float4 sg = make_float4(logistic(t4.x), logistic(t4.y), logistic(t4.z), logistic(t4.w));
+      if (MODE == 1) {
+        reinterpret_cast<float4 *>(static_cast<float *>(p.out) + (int64_t)prog * p.n_pad)[j4[q]] =
+            sg;
+      } else {
+        __nv_bfloat162 lo = __floats2bfloat162_rn(sg.x, sg.y);
+        __nv_bfloat162 hi = __floats2bfloat162_rn(sg.z, sg.w);
+        uint2 packed;
+        packed.x = *reinterpret_cast<uint32_t *>(&lo);
+        packed.y = *reinterpret_cast<uint32_t *>(&hi);
+        reinterpret_cast<uint2 *>(static_cast<__nv_bfloat16 *>(p.out) + (int64_t)prog * p.n_pad)
+            [j4[q]] = packed;
+      }
     }
   }
 }
 
+template <int MODE, int VEC>
+static cudaError_t interpret_launch(const InterpParams &p, int count, cudaStream_t s) {
+  const size_t smem = (size_t)p.stack_slots * VEC * kInterpThreads * sizeof(float4) +
+                      (size_t)p.max_len * sizeof(int2);
+  const int64_t tile = (int64_t)kInterpTile * VEC;
+  const dim3 grid((unsigned)count, (unsigned)((p.n_pad + tile - 1) / tile));
+  cudaError_t e = cudaFuncSetAttribute(interpret_kernel<MODE, VEC>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  interpret_kernel<MODE, VEC><<<grid, kInterpThreads, smem, s>>>(p);
+  return cudaGetLastError();
+}
+
+// Programs this long take two chunks per CTA (one decode per 8 cases).
+constexpr int kInterpWideGenes = 256;
+
 cudaError_t launch_interpret(int mode, const InterpParams &p, int count, cudaStream_t s) {
   if (count <= 0) return cudaSuccess;
-  const size_t smem = (size_t)p.stack_slots * kInterpThreads * sizeof(float4) +
-                      (size_t)p.max_len * sizeof(int2);
   // feature offsets are 32-bit float4 indices
   if (p.n_features <= 0 || (int64_t)p.n_features * (p.n_pad / 4) > (int64_t)INT32_MAX)
     return cudaErrorInvalidValue;
-  dim3 grid((unsigned)count, (unsigned)((p.n_pad + kInterpTile - 1) / kInterpTile));
-  cudaError_t e = cudaSuccess;
+  const bool wide = p.max_len >= kInterpWideGenes;
   switch (mode) {
-    case 0:
-      e = cudaFuncSetAttribute(interpret_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)smem);
-      if (e == cudaSuccess) interpret_kernel<0><<<grid, kInterpThreads, smem, s>>>(p);
-      break;
-    case 1:
-      e = cudaFuncSetAttribute(interpret_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)smem);
-      if (e == cudaSuccess) interpret_kernel<1><<<grid, kInterpThreads, smem, s>>>(p);
-      break;
-    default:
-      e = cudaFuncSetAttribute(interpret_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)smem);
-      if (e == cudaSuccess) interpret_kernel<2><<<grid, kInterpThreads, smem, s>>>(p);
-      break;
+    case 0: return wide ? interpret_launch<0, 2>(p, count, s) : interpret_launch<0, 1>(p, count, s);
+    case 1: return wide ? interpret_launch<1, 2>(p, count, s) : interpret_launch<1, 1>(p, count, s);
+    default: return wide ? interpret_launch<2, 2>(p, count, s) : interpret_launch<2, 1>(p, count, s);
   }
-  if (e != cudaSuccess) return e;
-  return cudaGetLastError();
 }
 
 // ComputeFitness of the initial population: one warp per individual sums
