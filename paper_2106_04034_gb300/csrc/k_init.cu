@@ -645,8 +645,10 @@ static cudaError_t interpret_launch(const InterpParams &p, int count, cudaStream
   return cudaGetLastError();
 }
 
-// Programs this long take two chunks per CTA (one decode per 8 cases).
-constexpr int kInterpWideGenes = 256;
+// Pools whose longest program has this many genes take two chunks per CTA
+// (one decode per 8 cases); shorter ones one chunk (measured on the paper's
+// k = 127 shape: 15.6 ms against 18.1 with one chunk).
+constexpr int kInterpWideGenes = 64;
 
 cudaError_t launch_interpret(int mode, const InterpParams &p, int count, cudaStream_t s) {
   if (count <= 0) return cudaSuccess;
