@@ -643,8 +643,15 @@ def main():
 
     if world > 1:
         import torch
+
+        from paper_2106_04034_gb300.build import build_library
         torch.cuda.set_device(local_rank)
         torch.distributed.init_process_group("nccl")
+        # one process per node builds (or finds current) the library before
+        # the others load it
+        if local_rank == 0:
+            build_library()
+        torch.distributed.barrier()
     if args.workload == "batched":
         line, ws = run_batched(args, rank, world, local_rank)
         # the oracle on the smallest run of the batch
