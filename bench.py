@@ -305,15 +305,18 @@ def run_ours(args, rank, world, local_rank):
     roofline = interp_roofline if float(interp_ms.sum()) > stream_ms_step else stream_roofline
     secondary = stream_roofline if roofline is interp_roofline else interp_roofline
 
-    # end to end through host buffers: host->device copies of the cases,
-    # the whole run, prediction copied back to the host
+    # end to end through host buffers: host->device copies of the cases from
+    # pinned host memory, the whole run, prediction copied back to the host
+    pinned = [torch.from_numpy(a).pin_memory() for a in (Xtr, ytr, Xte, yte)]
+    hXtr, hytr, hXte, hyte = (t.numpy() for t in pinned)
+
     def step_host():
-        run.load(Xtr, ytr, Xte, yte)
+        run.load(hXtr, hytr, hXte, hyte)
         run.init()
         run.evolve(G, log=False)
         if not w.p_crossover:
             run.best_trace()
-        return run.predict(Xte)
+        return run.predict(hXte)
 
     step_host()
     barrier()
@@ -475,13 +478,15 @@ def run_batched(args, rank, world, local_rank):
     ms_seq = timed(step_sequential, seq_steps)
     value_seq = job_value(updates, world, ms_seq / 1e3)
 
-    # end to end through host buffers
+    # end to end through host buffers (pinned host memory)
+    hdatas = [[torch.from_numpy(a).pin_memory().numpy() for a in d] for d in datas]
+
     def step_host():
-        for r, d in zip(runs, datas):
+        for r, d in zip(runs, hdatas):
             r.load(*d)
             r.init()
         batch.evolve(G, log=False)
-        return [r.predict(d[2]) for r, d in zip(runs, datas)]
+        return [r.predict(d[2]) for r, d in zip(runs, hdatas)]
 
     step_host()
     barrier()

@@ -152,6 +152,8 @@ gsgp_status gsgp_create(const gsgp_config *cfg, gsgp_ctx **out);
  * float32, y_* one float32 target per case.  Training cases drive selection;
  * test cases (n_test may be 0, pointers then NULL) are evaluated for every
  * individual.  The library copies them to the device, stored feature-major.
+ * Values are checked for NaN / Inf on the device after the copy; a rejected
+ * call leaves the previously loaded data in place.  Synchronises the stream.
  * Errors: GSGP_E_INVALID (n_train < 1, n_features < 1 or > 65535,
  * NULL data, any non-finite value), GSGP_E_OOM, GSGP_E_CUDA. */
 gsgp_status gsgp_load(gsgp_ctx *ctx, const float *X_train, const float *y_train,

@@ -236,12 +236,6 @@ gsgp_status use_device(gsgp_ctx *c) {
 }
 
 // ------------------------------------------------------------------ load --
-static bool host_finite(const float *v, int64_t n) {
-  for (int64_t i = 0; i < n; ++i)
-    if (!std::isfinite(v[i])) return false;
-  return true;
-}
-
 static gsgp_status check_shapes(gsgp_ctx *c, const float *Xtr, const float *ytr, int64_t ntr,
                                 int32_t l, const float *Xte, const float *yte, int64_t nte) {
   if (ntr < 1) return fail(c, GSGP_E_INVALID, "n_train must be >= 1");
@@ -280,25 +274,38 @@ extern "C" gsgp_status gsgp_load(gsgp_ctx *c, const float *Xtr, const float *ytr
                                  int32_t l, const float *Xte, const float *yte, int64_t nte) {
   API_GUARD(c)
   TRY(check_shapes(c, Xtr, ytr, ntr, l, Xte, yte, nte));
-  if (!host_finite(Xtr, ntr * l) || !host_finite(ytr, ntr) ||
-      (nte > 0 && (!host_finite(Xte, nte * l) || !host_finite(yte, nte))))
-    return fail(c, GSGP_E_INVALID, "non-finite value in the fitness cases");
-  TRY(prepare_data(c, ntr, l, nte));
+  TRY(use_device(c));
+  // stage every input on the device and check it there (a scan on the GPU
+  // instead of the host), before the context's data is touched
+  const size_t nx_tr = (size_t)ntr * l, nx_te = (size_t)nte * l;
   float *stage = nullptr;
-  const int64_t rows = ntr > nte ? ntr : nte;
-  TRY(dalloc_n(c, &stage, (size_t)rows * l));
-  CK(cudaMemcpyAsync(stage, Xtr, sizeof(float) * (size_t)ntr * l, cudaMemcpyHostToDevice,
-                     c->stream));
-  LAUNCH(1, launch_transpose(stage, ntr, l, c->X, c->n_pad, 0, c->stream));
-  CK(cudaMemcpyAsync(c->t, ytr, sizeof(float) * (size_t)ntr, cudaMemcpyHostToDevice, c->stream));
+  TRY(dalloc_n(c, &stage, nx_tr + nx_te + (size_t)ntr + (size_t)nte));
+  struct Free {
+    gsgp_ctx *c;
+    float *&p;
+    ~Free() { dfree(c, p); }
+  } guard{c, stage};
+  float *sXtr = stage, *sXte = stage + nx_tr, *sy = stage + nx_tr + nx_te;
+  CK(cudaMemcpyAsync(sXtr, Xtr, sizeof(float) * nx_tr, cudaMemcpyHostToDevice, c->stream));
+  CK(cudaMemcpyAsync(sy, ytr, sizeof(float) * (size_t)ntr, cudaMemcpyHostToDevice, c->stream));
   if (nte > 0) {
-    CK(cudaMemcpyAsync(stage, Xte, sizeof(float) * (size_t)nte * l, cudaMemcpyHostToDevice,
-                       c->stream));
-    LAUNCH(1, launch_transpose(stage, nte, l, c->X, c->n_pad, ntr, c->stream));
-    CK(cudaMemcpyAsync(c->t + ntr, yte, sizeof(float) * (size_t)nte, cudaMemcpyHostToDevice,
+    CK(cudaMemcpyAsync(sXte, Xte, sizeof(float) * nx_te, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(sy + ntr, yte, sizeof(float) * (size_t)nte, cudaMemcpyHostToDevice,
                        c->stream));
   }
-  dfree(c, stage);
+  if (!c->d_flag) TRY(dalloc_n(c, &c->d_flag, 1));
+  CK(cudaMemsetAsync(c->d_flag, 0, sizeof(unsigned), c->stream));
+  LAUNCH(1, launch_nonfinite_check(stage, (int64_t)(nx_tr + nx_te + ntr + nte), c->d_flag,
+                                   c->stream));
+  unsigned bad = 0;
+  CK(cudaMemcpyAsync(&bad, c->d_flag, sizeof bad, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  if (bad) return fail(c, GSGP_E_INVALID, "non-finite value in the fitness cases");
+  TRY(prepare_data(c, ntr, l, nte));
+  LAUNCH(1, launch_transpose(sXtr, ntr, l, c->X, c->n_pad, 0, c->stream));
+  CK(cudaMemcpyAsync(c->t, sy, sizeof(float) * (size_t)(ntr + nte), cudaMemcpyDeviceToDevice,
+                     c->stream));
+  if (nte > 0) LAUNCH(1, launch_transpose(sXte, nte, l, c->X, c->n_pad, ntr, c->stream));
   return GSGP_OK;
   API_END(c)
 }
@@ -1297,21 +1304,35 @@ extern "C" gsgp_status gsgp_predict(gsgp_ctx *c, const float *X, int64_t n, doub
   if (c->state != 2) return fail(c, GSGP_E_STATE, "gsgp_predict before gsgp_init");
   if (n < 0 || (n > 0 && (!X || !y_out))) return fail(c, GSGP_E_INVALID, "bad predict arguments");
   if (n == 0) return GSGP_OK;
-  if (!host_finite(X, n * c->l)) return fail(c, GSGP_E_INVALID, "non-finite value in X");
   TRY(use_device(c));
+  struct Bufs {
+    gsgp_ctx *c;
+    float *Xd = nullptr;
+    double *yd = nullptr;
+    ~Bufs() {
+      dfree(c, Xd);
+      dfree(c, yd);
+    }
+  } b{c};
+  TRY(dalloc_n(c, &b.Xd, (size_t)n * c->l));
+  TRY(dalloc_n(c, &b.yd, (size_t)n));
+  CK(cudaMemcpyAsync(b.Xd, X, sizeof(float) * (size_t)n * c->l, cudaMemcpyHostToDevice,
+                     c->stream));
+  // the cases are checked on the device once copied
+  if (!c->d_flag) TRY(dalloc_n(c, &c->d_flag, 1));
+  CK(cudaMemsetAsync(c->d_flag, 0, sizeof(unsigned), c->stream));
+  LAUNCH(1, launch_nonfinite_check(b.Xd, n * c->l, c->d_flag, c->stream));
+  unsigned bad = 0;
+  CK(cudaMemcpyAsync(&bad, c->d_flag, sizeof bad, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  if (bad) return fail(c, GSGP_E_INVALID, "non-finite value in X");
   if (!with_crossover(c)) TRY(build_model(c));
-  float *Xd = nullptr;
-  double *yd = nullptr;
-  TRY(dalloc_n(c, &Xd, (size_t)n * c->l));
-  TRY(dalloc_n(c, &yd, (size_t)n));
-  CK(cudaMemcpyAsync(Xd, X, sizeof(float) * (size_t)n * c->l, cudaMemcpyHostToDevice, c->stream));
   if (with_crossover(c))
-    TRY(run_predict_replay(c, Xd, n, yd));
+    TRY(run_predict_replay(c, b.Xd, n, b.yd));
   else
-    TRY(run_predict(c, Xd, n, yd));
-  CK(cudaMemcpyAsync(y_out, yd, sizeof(double) * (size_t)n, cudaMemcpyDeviceToHost, c->stream));
-  dfree(c, Xd);
-  dfree(c, yd);
+    TRY(run_predict(c, b.Xd, n, b.yd));
+  CK(cudaMemcpyAsync(y_out, b.yd, sizeof(double) * (size_t)n, cudaMemcpyDeviceToHost,
+                     c->stream));
   CK(cudaStreamSynchronize(c->stream));
   return GSGP_OK;
   API_END(c)

@@ -100,12 +100,13 @@ def test_state_machine_without_device(lib):
     r.close()   # idempotent
 
 
+# Non-finite values are checked on the device once the cases are copied
+# there (tests/test_gpu_parity.py); shapes are checked on the host first.
 @pytest.mark.parametrize("args", [
     dict(X=np.zeros((0, 3)), y=np.zeros(0)),                  # no training case
-    dict(X=np.array([[1.0, np.inf]]), y=np.zeros(1)),          # non-finite feature
-    dict(X=np.zeros((2, 2)), y=np.array([0.0, np.nan])),       # non-finite target
+    dict(X=np.zeros((2, 0)), y=np.zeros(2)),                  # no feature
 ])
-def test_bad_data_is_rejected_on_the_host(lib, args):
+def test_bad_shapes_are_rejected_on_the_host(lib, args):
     r = pkg.Run(pop_size=8, n_random_trees=4)
     with pytest.raises(pkg.GsgpError) as e:
         r.load(args["X"], args["y"])

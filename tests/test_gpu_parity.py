@@ -379,3 +379,29 @@ def test_default_path_is_persistent():
     assert info.evolve_path == pkg.PATH_PERSISTENT and info.evolve_grid >= 1
     assert info.evolve_offspring_per_cta > 0     # the autotuner picks a register-stream shape
     run.close()
+
+
+def test_non_finite_host_inputs_are_rejected_on_the_device():
+    """gsgp_load and gsgp_predict check host inputs after copying them to the
+    device; a rejected load leaves the loaded data and the run untouched."""
+    w = TINY
+    data = W.make_data(w)
+    run, _, _ = gpu_run(w, data=data)
+    ref, _, _ = gpu_run(w, data=data)
+    for k, v in ((0, np.nan), (1, np.inf), (2, -np.inf), (3, np.nan)):
+        bad = [a.copy() for a in data]
+        bad[k].reshape(-1)[len(bad[k].reshape(-1)) // 2] = v
+        with pytest.raises(pkg.GsgpError):
+            run.load(*bad)
+    run.evolve(4, log=False)
+    ref.evolve(4, log=False)
+    assert np.array_equal(run.semantics(pkg.POOL_POPULATION), ref.semantics(pkg.POOL_POPULATION))
+    Xn = W.make_new_cases(w, 50)
+    y = run.predict(Xn)
+    Xn[7, 0] = np.nan
+    with pytest.raises(pkg.GsgpError):
+        run.predict(Xn)
+    Xn[7, 0] = 0.5
+    assert np.all(np.isfinite(run.predict(Xn))) and np.all(np.isfinite(y))
+    run.close()
+    ref.close()
