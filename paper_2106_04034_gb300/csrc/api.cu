@@ -1581,6 +1581,15 @@ extern "C" void gsgp_destroy(gsgp_ctx *c) {
     dfree(c, c->X);
     dfree(c, c->t);
     dfree(c, c->d_flag);
+    // anything an interrupted call left behind (an error between its
+    // allocation and its release)
+    for (const auto &kv : c->allocs) {
+      if (c->cfg.alloc)
+        c->cfg.free(c->cfg.alloc_user, kv.first, c->stream);
+      else
+        cudaFreeAsync(kv.first, c->stream);
+    }
+    c->allocs.clear();
     for (auto e : c->ev0) cudaEventDestroy(e);
     for (auto e : c->ev_marks) cudaEventDestroy(e);
     for (auto e : c->ev1) cudaEventDestroy(e);
