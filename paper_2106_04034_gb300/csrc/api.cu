@@ -1214,6 +1214,8 @@ static gsgp_status run_predict_replay(gsgp_ctx *c, const float *X_dev_rows, int6
                                       double *y_dev) {
   const int m = c->cfg.pop_size, r = c->cfg.n_random_trees, G = c->gen;
   const int64_t n_pad = (n + 3) / 4 * 4;
+  if ((int64_t)G * m > (int64_t)INT32_MAX)   // slot lists are indexed with 32 bits
+    return fail(c, GSGP_E_INVALID, "trace of %d generations x %d slots too long to replay", G, m);
   struct Bufs {
     gsgp_ctx *c;
     float *Xt = nullptr;
