@@ -263,6 +263,8 @@ __global__ void __launch_bounds__(kGenThreads, 4) persist_kernel(const GenParams
   constexpr int NW = kGenThreads / 32;
   constexpr int W = 1024 * VEC;
   __shared__ ItemSums<VEC, OPB> s_sum[2];   // sub-block totals, double-buffered per item
+  __shared__ int4 s_isel[2][OPB];           // draws of the current / next item (VEC = 1)
+  __shared__ float s_ims[2][OPB];
   __shared__ ulonglong2 s_min[32], s_max[32];
   __shared__ double2 s_sse[NW];
   __shared__ int s_ok;
@@ -297,7 +299,35 @@ __global__ void __launch_bounds__(kGenThreads, 4) persist_kernel(const GenParams
     // ---------------- M: mutation stream ----------------------------------
     // CTA b streams items b, b + grid, ... in tile-major order; the grid is
     // sized so that every CTA gets the same number of items.
-    {
+    if constexpr (VEC == 1 && !CROSS) {
+      // 1024-case tiles: the draws of each item in shared memory, one item
+      // ahead, and the row loads pipelined one offspring ahead
+      int buf = 0;
+      if (tid < OPB && b < items) {
+        const int i = (b % groups) * OPB + tid;
+        if (i < m) {
+          s_isel[0][tid] = __ldcg(p.sel + i);
+          s_ims[0][tid] = __ldcg(p.sel_ms + i);
+        }
+      }
+      __syncthreads();
+      for (int item = b; item < items; item += nb, buf ^= 1) {
+        const int tile = item / groups;
+        const int i0 = (item - tile * groups) * OPB;
+        const int cnt = min(OPB, m - i0);
+        if (tid < OPB && item + nb < items) {
+          const int i = ((item + nb) % groups) * OPB + tid;
+          if (i < m) {
+            s_isel[buf ^ 1][tid] = __ldcg(p.sel + i);
+            s_ims[buf ^ 1][tid] = __ldcg(p.sel_ms + i);
+          }
+        }
+        stream_item_pipe<SigT, OPB>(p, tile, cnt, s_isel[buf], s_ims[buf], s_sum[buf]);
+        // one barrier per item: it also publishes the next item's draws
+        __syncthreads();
+        item_partials<VEC, OPB>(p, tile, i0, cnt, s_sum[buf]);
+      }
+    } else {
       int buf = 0;   // alternates per item
       // the first draws of the next item are loaded one item ahead
       int4 sel_next = make_int4(0, 0, 0, 0);

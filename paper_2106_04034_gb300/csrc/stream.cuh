@@ -278,6 +278,64 @@ __device__ __forceinline__ void stream_item(const GenParams &p, int tile, int i0
   }
 }
 
+// Mutation stream of one item with 1024-case tiles (VEC = 1), software
+// pipelined: the next offspring's parent and random-tree loads are issued
+// before the current offspring's arithmetic, store and reduction, and the
+// targets are read once per item.  The item's draws come from shared memory
+// (sels / mss, filled one item ahead), so no offspring waits for its draws.
+// The arithmetic and the sub-block sums are mutate4's and stream_item's.
+template <typename SigT, int OPB>
+__device__ __forceinline__ void stream_item_pipe(const GenParams &p, int tile, int cnt,
+                                                 const int4 *sels, const float *mss,
+                                                 ItemSums<1, OPB> &sum) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const SigT *sig = static_cast<const SigT *>(p.sigma_r);
+  const int64_t j0 = (int64_t)tile * 1024 + tid * 4;
+  const bool in = j0 < p.n_pad;
+  const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+  float4 t4 = zero, s = zero, a = zero, bb = zero;
+  if (in) {
+    t4 = __ldg(reinterpret_cast<const float4 *>(p.target + j0));
+    const int4 e = sels[0];
+    s = __ldcg(reinterpret_cast<const float4 *>(p.pool + (int64_t)e.x * p.n_pad + j0));
+    a = SigLoad<SigT>::load(sig + (int64_t)e.z * p.n_pad, j0);
+    bb = SigLoad<SigT>::load(sig + (int64_t)e.w * p.n_pad, j0);
+  }
+  for (int k = 0; k < cnt; ++k) {
+    const int orow = sels[k].y;
+    const float step = mss[k];
+    float4 s2 = s, a2 = a, b2 = bb;   // the next offspring's operands
+    if (in && k + 1 < cnt) {
+      const int4 en = sels[k + 1];
+      s2 = __ldcg(reinterpret_cast<const float4 *>(p.pool + (int64_t)en.x * p.n_pad + j0));
+      a2 = SigLoad<SigT>::load(sig + (int64_t)en.z * p.n_pad, j0);
+      b2 = SigLoad<SigT>::load(sig + (int64_t)en.w * p.n_pad, j0);
+    }
+    float str = 0.f, ste = 0.f;
+    if (in) {
+      float4 o;
+      o.x = fmaf(step, a.x - bb.x, s.x);
+      o.y = fmaf(step, a.y - bb.y, s.y);
+      o.z = fmaf(step, a.z - bb.z, s.z);
+      o.w = fmaf(step, a.w - bb.w, s.w);
+      *reinterpret_cast<float4 *>(p.pool + (int64_t)orow * p.n_pad + j0) = o;
+      const float dd[4] = {o.x - t4.x, o.y - t4.y, o.z - t4.z, o.w - t4.w};
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        if (j0 + q < p.n_train)
+          str += dd[q] * dd[q];
+        else if (j0 + q < p.n_cases)
+          ste += dd[q] * dd[q];
+      }
+    }
+    const float2 t = subblock_sum(str, ste);
+    if (lane == 0) sum[k][0][warp] = t;
+    s = s2;
+    a = a2;
+    bb = b2;
+  }
+}
+
 // Chunk partials of one stream item from its sub-block totals (after a
 // barrier that follows stream_item).
 template <int VEC, int OPB>
