@@ -413,8 +413,9 @@ gsgp_status gsgp_batch_evolve(gsgp_batch *batch, int32_t generations, double *be
                               double *best_test_rmse);
 
 /* Shape of the batch's mutation stream: tiles of 1024 * vec cases for opb
- * offspring per CTA, vec in {1, 2}, opb in {1, 2, 4}; (0, 0), the default,
- * autotunes.  Results do not depend on the shape.  Errors: GSGP_E_INVALID. */
+ * offspring per CTA, vec in {1, 2} with opb in {1, 2, 4}, or vec 1 with opb 8;
+ * (0, 0), the default, autotunes.  Results do not depend on the shape.
+ * Errors: GSGP_E_INVALID. */
 gsgp_status gsgp_batch_set_shape(gsgp_batch *batch, int32_t vec, int32_t opb);
 
 /* Kernel timing of the batch, as gsgp_set_kernel_timing / gsgp_kernel_times:

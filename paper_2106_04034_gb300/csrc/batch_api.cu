@@ -231,7 +231,7 @@ gsgp_status build_graph(gsgp_batch *b) {
   return GSGP_OK;
 }
 
-const GenShape kBatchShapes[] = {{1, 1}, {1, 2}, {1, 4}, {2, 1}, {2, 2}, {2, 4}};
+const GenShape kBatchShapes[] = {{1, 1}, {1, 2}, {1, 4}, {1, 8}, {2, 1}, {2, 2}, {2, 4}};
 
 // One generation of the whole batch in shape sh, timed, with every run's
 // state restored afterwards (the trial rewrites only what the real
@@ -382,7 +382,8 @@ extern "C" gsgp_status gsgp_batch_set_shape(gsgp_batch *b, int32_t vec, int32_t 
   BATCH_GUARD(b)
   const bool autotune = vec == 0 && opb == 0;
   if (!autotune && !batch_shape_supported(GenShape{vec, opb}))
-    return bfail(b, GSGP_E_INVALID, "batch shape must have vec in {1,2} and opb in {1,2,4}");
+    return bfail(b, GSGP_E_INVALID,
+                 "batch shape must have vec in {1,2} and opb in {1,2,4}, or vec 1 and opb 8");
   b->forced = autotune ? GenShape{0, 0} : GenShape{vec, opb};
   b->shape_ready = false;
   return GSGP_OK;

@@ -41,6 +41,8 @@ template <typename SigT, int VEC, int OPB, bool CROSS>
 __global__ void __launch_bounds__(kGenThreads, 4) batch_kernel(const __grid_constant__ BatchArgs a) {
   constexpr int NW = kGenThreads / 32;
   __shared__ ItemSums<VEC, OPB> s_sum[2];
+  __shared__ int4 s_isel[2][OPB];   // draws of the current / next item (VEC = 1)
+  __shared__ float s_ims[2][OPB];
   __shared__ int s_ok;
 
   GridSync *gs = a.gs;
@@ -64,7 +66,36 @@ __global__ void __launch_bounds__(kGenThreads, 4) batch_kernel(const __grid_cons
     if (!grid_sync(gs, epoch, &s_ok)) return;
 
     // ---------------- M: mutation stream ----------------------------------
-    {
+    if constexpr (VEC == 1 && !CROSS) {
+      // 1024-case tiles: each item's draws staged in shared memory one item
+      // ahead, the row loads pipelined one offspring ahead
+      int buf = 0, r = 0, rn = 0;
+      auto stage = [&](int item, int to) {
+        rn = advance_run(a.item_off, rn, item);
+        const GenParams &q = a.runs[rn];
+        const int groups = (q.m + OPB - 1) / OPB;
+        const int i = ((item - a.item_off[rn]) % groups) * OPB + tid;
+        if (tid < OPB && i < q.m) {
+          s_isel[to][tid] = __ldcg(q.sel + i);
+          s_ims[to][tid] = __ldcg(q.sel_ms + i);
+        }
+      };
+      if (b < items) stage(b, 0);
+      __syncthreads();
+      for (int item = b; item < items; item += nb, buf ^= 1) {
+        r = advance_run(a.item_off, r, item);
+        const GenParams &p = a.runs[r];
+        const int groups = (p.m + OPB - 1) / OPB;
+        const int local = item - a.item_off[r];
+        const int tile = local / groups;
+        const int i0 = (local - tile * groups) * OPB;
+        const int cnt = min(OPB, p.m - i0);
+        if (item + nb < items) stage(item + nb, buf ^ 1);
+        stream_item_pipe<SigT, OPB>(p, tile, cnt, s_isel[buf], s_ims[buf], s_sum[buf]);
+        __syncthreads();   // one barrier per item; it also publishes the next item's draws
+        item_partials<VEC, OPB>(p, tile, i0, cnt, s_sum[buf]);
+      }
+    } else {
       // the first draws of the next item are loaded one item ahead
       int buf = 0, r = 0, rn = 0;
       int4 sel_next = make_int4(0, 0, 0, 0);
@@ -138,6 +169,7 @@ static const void *batch_pick(int sigma_bf16, const GenShape &sh, bool cross = f
   GSGP_BATCH_CASE(1, 1)
   GSGP_BATCH_CASE(1, 2)
   GSGP_BATCH_CASE(1, 4)
+  GSGP_BATCH_CASE(1, 8)
   GSGP_BATCH_CASE(2, 1)
   GSGP_BATCH_CASE(2, 2)
   GSGP_BATCH_CASE(2, 4)

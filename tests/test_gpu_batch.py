@@ -98,7 +98,7 @@ def test_batch_equals_single_runs(singles):
         r.close()
 
 
-@pytest.mark.parametrize("vec,opb", [(1, 1), (1, 2), (1, 4), (2, 1), (2, 2), (2, 4)])
+@pytest.mark.parametrize("vec,opb", [(1, 1), (1, 2), (1, 4), (1, 8), (2, 1), (2, 2), (2, 4)])
 def test_every_batch_shape_gives_identical_results(singles, vec, opb):
     runs = make_runs()
     batch = pkg.Batch([r for r, _, _ in runs])
