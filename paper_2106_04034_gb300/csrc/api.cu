@@ -837,7 +837,9 @@ static gsgp_status choose_shape(gsgp_ctx *c) {
         if (path == 1 && persist_max_grid(bf, cand[k]) <= 0) continue;
         float ms = 0.f;
         TRY(time_shape(c, path, cand[k], &ms));
-        if (ms < best_ms) {
+        // a later shape must win by more than 1% (trial noise): near-ties
+        // keep the earlier shape, so the choice repeats from run to run
+        if (ms < best_ms * 0.99f) {
           best_ms = ms;
           best = Tuned{path, cand[k]};
         }

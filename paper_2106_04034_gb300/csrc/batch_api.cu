@@ -301,7 +301,7 @@ gsgp_status choose_shape(gsgp_batch *b) {
     for (const GenShape &sh : kBatchShapes) {
       float ms = 1e30f;
       BTRY(time_shape(b, sh, &ms));
-      if (ms < best_ms) {
+      if (ms < best_ms * 0.99f) {   // near-ties keep the earlier shape
         best_ms = ms;
         best = sh;
       }
