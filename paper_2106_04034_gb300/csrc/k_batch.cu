@@ -66,7 +66,7 @@ __global__ void __launch_bounds__(kGenThreads, 4) batch_kernel(const __grid_cons
     if (!grid_sync(gs, epoch, &s_ok)) return;
 
     // ---------------- M: mutation stream ----------------------------------
-    if constexpr (VEC == 1 && !CROSS) {
+    if constexpr (VEC == 1) {
       // 1024-case tiles: each item's draws staged in shared memory one item
       // ahead, the row loads pipelined one offspring ahead
       int buf = 0, r = 0, rn = 0;
@@ -91,7 +91,7 @@ __global__ void __launch_bounds__(kGenThreads, 4) batch_kernel(const __grid_cons
         const int i0 = (local - tile * groups) * OPB;
         const int cnt = min(OPB, p.m - i0);
         if (item + nb < items) stage(item + nb, buf ^ 1);
-        stream_item_pipe<SigT, OPB>(p, tile, cnt, s_isel[buf], s_ims[buf], s_sum[buf]);
+        stream_item_pipe<SigT, OPB, CROSS>(p, tile, cnt, s_isel[buf], s_ims[buf], s_sum[buf]);
         __syncthreads();   // one barrier per item; it also publishes the next item's draws
         item_partials<VEC, OPB>(p, tile, i0, cnt, s_sum[buf]);
       }

@@ -299,7 +299,7 @@ __global__ void __launch_bounds__(kGenThreads, 4) persist_kernel(const GenParams
     // ---------------- M: mutation stream ----------------------------------
     // CTA b streams items b, b + grid, ... in tile-major order; the grid is
     // sized so that every CTA gets the same number of items.
-    if constexpr (VEC == 1 && !CROSS) {
+    if constexpr (VEC == 1) {
       // 1024-case tiles: the draws of each item in shared memory, one item
       // ahead, and the row loads pipelined one offspring ahead
       int buf = 0;
@@ -322,7 +322,7 @@ __global__ void __launch_bounds__(kGenThreads, 4) persist_kernel(const GenParams
             s_ims[buf ^ 1][tid] = __ldcg(p.sel_ms + i);
           }
         }
-        stream_item_pipe<SigT, OPB>(p, tile, cnt, s_isel[buf], s_ims[buf], s_sum[buf]);
+        stream_item_pipe<SigT, OPB, CROSS>(p, tile, cnt, s_isel[buf], s_ims[buf], s_sum[buf]);
         // one barrier per item: it also publishes the next item's draws
         __syncthreads();
         item_partials<VEC, OPB>(p, tile, i0, cnt, s_sum[buf]);

@@ -278,13 +278,16 @@ __device__ __forceinline__ void stream_item(const GenParams &p, int tile, int i0
   }
 }
 
-// Mutation stream of one item with 1024-case tiles (VEC = 1), software
-// pipelined: the next offspring's parent and random-tree loads are issued
-// before the current offspring's arithmetic, store and reduction, and the
-// targets are read once per item.  The item's draws come from shared memory
-// (sels / mss, filled one item ahead), so no offspring waits for its draws.
-// The arithmetic and the sub-block sums are mutate4's and stream_item's.
-template <typename SigT, int OPB>
+// Stream of one item with 1024-case tiles (VEC = 1), software pipelined:
+// the next offspring's three row loads are issued before the current
+// offspring's arithmetic, store and reduction, and the targets are read
+// once per item.  The item's draws come from shared memory (sels / mss,
+// filled one item ahead), so no offspring waits for its draws.  A mutation
+// loads its parent and two random-tree rows, a crossover (CROSS, entry
+// w = -1 - second parent row) its two parents and the mask tree; the
+// arithmetic and the sub-block sums are mutate4's / crossover4's and
+// stream_item's.
+template <typename SigT, int OPB, bool CROSS>
 __device__ __forceinline__ void stream_item_pipe(const GenParams &p, int tile, int cnt,
                                                  const int4 *sels, const float *mss,
                                                  ItemSums<1, OPB> &sum) {
@@ -293,32 +296,41 @@ __device__ __forceinline__ void stream_item_pipe(const GenParams &p, int tile, i
   const int64_t j0 = (int64_t)tile * 1024 + tid * 4;
   const bool in = j0 < p.n_pad;
   const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
-  float4 t4 = zero, s = zero, a = zero, bb = zero;
+  // x: parent row; y: random tree a (mutation) or mask tree (crossover);
+  // z: random tree b (mutation) or second parent row (crossover)
+  auto load = [&](const int4 e, float4 &x, float4 &y, float4 &z) {
+    x = __ldcg(reinterpret_cast<const float4 *>(p.pool + (int64_t)e.x * p.n_pad + j0));
+    y = SigLoad<SigT>::load(sig + (int64_t)e.z * p.n_pad, j0);
+    if (CROSS && e.w < 0)
+      z = __ldcg(reinterpret_cast<const float4 *>(p.pool + (int64_t)(-1 - e.w) * p.n_pad + j0));
+    else
+      z = SigLoad<SigT>::load(sig + (int64_t)e.w * p.n_pad, j0);
+  };
+  float4 t4 = zero, x = zero, y = zero, z = zero;
   if (in) {
     t4 = __ldg(reinterpret_cast<const float4 *>(p.target + j0));
-    const int4 e = sels[0];
-    s = __ldcg(reinterpret_cast<const float4 *>(p.pool + (int64_t)e.x * p.n_pad + j0));
-    a = SigLoad<SigT>::load(sig + (int64_t)e.z * p.n_pad, j0);
-    bb = SigLoad<SigT>::load(sig + (int64_t)e.w * p.n_pad, j0);
+    load(sels[0], x, y, z);
   }
   for (int k = 0; k < cnt; ++k) {
-    const int orow = sels[k].y;
+    const int4 e = sels[k];
     const float step = mss[k];
-    float4 s2 = s, a2 = a, b2 = bb;   // the next offspring's operands
-    if (in && k + 1 < cnt) {
-      const int4 en = sels[k + 1];
-      s2 = __ldcg(reinterpret_cast<const float4 *>(p.pool + (int64_t)en.x * p.n_pad + j0));
-      a2 = SigLoad<SigT>::load(sig + (int64_t)en.z * p.n_pad, j0);
-      b2 = SigLoad<SigT>::load(sig + (int64_t)en.w * p.n_pad, j0);
-    }
+    float4 x2 = x, y2 = y, z2 = z;   // the next offspring's operands
+    if (in && k + 1 < cnt) load(sels[k + 1], x2, y2, z2);
     float str = 0.f, ste = 0.f;
     if (in) {
       float4 o;
-      o.x = fmaf(step, a.x - bb.x, s.x);
-      o.y = fmaf(step, a.y - bb.y, s.y);
-      o.z = fmaf(step, a.z - bb.z, s.z);
-      o.w = fmaf(step, a.w - bb.w, s.w);
-      *reinterpret_cast<float4 *>(p.pool + (int64_t)orow * p.n_pad + j0) = o;
+      if (CROSS && e.w < 0) {   // R T1 + (1 - R) T2 as T2 + R (T1 - T2)
+        o.x = fmaf(y.x, x.x - z.x, z.x);
+        o.y = fmaf(y.y, x.y - z.y, z.y);
+        o.z = fmaf(y.z, x.z - z.z, z.z);
+        o.w = fmaf(y.w, x.w - z.w, z.w);
+      } else {
+        o.x = fmaf(step, y.x - z.x, x.x);
+        o.y = fmaf(step, y.y - z.y, x.y);
+        o.z = fmaf(step, y.z - z.z, x.z);
+        o.w = fmaf(step, y.w - z.w, x.w);
+      }
+      *reinterpret_cast<float4 *>(p.pool + (int64_t)e.y * p.n_pad + j0) = o;
       const float dd[4] = {o.x - t4.x, o.y - t4.y, o.z - t4.z, o.w - t4.w};
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
@@ -330,9 +342,9 @@ __device__ __forceinline__ void stream_item_pipe(const GenParams &p, int tile, i
     }
     const float2 t = subblock_sum(str, ste);
     if (lane == 0) sum[k][0][warp] = t;
-    s = s2;
-    a = a2;
-    bb = b2;
+    x = x2;
+    y = y2;
+    z = z2;
   }
 }
 
