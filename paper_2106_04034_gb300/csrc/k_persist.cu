@@ -34,6 +34,8 @@
 // CTAs are co-resident.  The selection runs on the first CTAs and the
 // persisting of the slot-to-row map on the last ones, so that CTAs arrive at
 // the barriers spread out in time rather than all at once.
+#include <type_traits>
+
 #include "gridsync.cuh"
 #include "kernels.cuh"
 #include "reduce.cuh"
@@ -299,9 +301,11 @@ __global__ void __launch_bounds__(kGenThreads, 4) persist_kernel(const GenParams
     // ---------------- M: mutation stream ----------------------------------
     // CTA b streams items b, b + grid, ... in tile-major order; the grid is
     // sized so that every CTA gets the same number of items.
-    if constexpr (VEC == 1) {
-      // 1024-case tiles: the draws of each item in shared memory, one item
-      // ahead, and the row loads pipelined one offspring ahead
+    constexpr bool kPipeBf16 = VEC == 2 && !CROSS && std::is_same<SigT, __nv_bfloat16>::value;
+    if constexpr (VEC == 1 || kPipeBf16) {
+      // 1024-case tiles (or bf16 sigma with 2048-case tiles): the draws of
+      // each item in shared memory, one item ahead, and the row loads
+      // pipelined one offspring ahead
       int buf = 0;
       if (tid < OPB && b < items) {
         const int i = (b % groups) * OPB + tid;
@@ -322,7 +326,10 @@ __global__ void __launch_bounds__(kGenThreads, 4) persist_kernel(const GenParams
             s_ims[buf ^ 1][tid] = __ldcg(p.sel_ms + i);
           }
         }
-        stream_item_pipe<SigT, OPB, CROSS>(p, tile, cnt, s_isel[buf], s_ims[buf], s_sum[buf]);
+        if constexpr (VEC == 1)
+          stream_item_pipe<SigT, OPB, CROSS>(p, tile, cnt, s_isel[buf], s_ims[buf], s_sum[buf]);
+        else
+          stream_item_pipe_bf16x2<OPB>(p, tile, cnt, s_isel[buf], s_ims[buf], s_sum[buf]);
         // one barrier per item: it also publishes the next item's draws
         __syncthreads();
         item_partials<VEC, OPB>(p, tile, i0, cnt, s_sum[buf]);

@@ -348,6 +348,86 @@ __device__ __forceinline__ void stream_item_pipe(const GenParams &p, int tile, i
   }
 }
 
+// The same pipelined stream for bf16 sigma and 2048-case tiles (VEC = 2),
+// mutation only: the next offspring's parent row and raw bf16 pairs are
+// loaded while the current offspring is computed (the bf16 values are
+// widened only when used, which keeps two offspring's operands within the
+// register budget).  Arithmetic and sums as mutate4 / stream_item.
+template <int OPB>
+__device__ __forceinline__ void stream_item_pipe_bf16x2(const GenParams &p, int tile, int cnt,
+                                                        const int4 *sels, const float *mss,
+                                                        ItemSums<2, OPB> &sum) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const __nv_bfloat16 *sig = static_cast<const __nv_bfloat16 *>(p.sigma_r);
+  const int64_t base = (int64_t)tile * 2048 + tid * 4;
+  const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+  const uint2 zero2 = make_uint2(0u, 0u);
+  auto widen = [](const uint2 u) {
+    return make_float4(__uint_as_float(u.x << 16), __uint_as_float(u.x & 0xffff0000u),
+                       __uint_as_float(u.y << 16), __uint_as_float(u.y & 0xffff0000u));
+  };
+  float4 t4[2], x[2];
+  uint2 y[2], z[2];
+#pragma unroll
+  for (int v = 0; v < 2; ++v) {
+    t4[v] = x[v] = zero;
+    y[v] = z[v] = zero2;
+  }
+  auto load = [&](const int4 e, float4 (&xx)[2], uint2 (&yy)[2], uint2 (&zz)[2]) {
+#pragma unroll
+    for (int v = 0; v < 2; ++v) {
+      const int64_t j0 = base + v * 1024;
+      if (j0 < p.n_pad) {
+        xx[v] = __ldcg(reinterpret_cast<const float4 *>(p.pool + (int64_t)e.x * p.n_pad + j0));
+        yy[v] = __ldg(reinterpret_cast<const uint2 *>(sig + (int64_t)e.z * p.n_pad + j0));
+        zz[v] = __ldg(reinterpret_cast<const uint2 *>(sig + (int64_t)e.w * p.n_pad + j0));
+      }
+    }
+  };
+#pragma unroll
+  for (int v = 0; v < 2; ++v)
+    if (base + v * 1024 < p.n_pad)
+      t4[v] = __ldg(reinterpret_cast<const float4 *>(p.target + base + v * 1024));
+  load(sels[0], x, y, z);
+  for (int k = 0; k < cnt; ++k) {
+    const int orow = sels[k].y;
+    const float step = mss[k];
+    float4 x2[2] = {x[0], x[1]};
+    uint2 y2[2] = {y[0], y[1]}, z2[2] = {z[0], z[1]};
+    if (k + 1 < cnt) load(sels[k + 1], x2, y2, z2);
+#pragma unroll
+    for (int v = 0; v < 2; ++v) {
+      const int64_t j0 = base + v * 1024;
+      float str = 0.f, ste = 0.f;
+      if (j0 < p.n_pad) {
+        const float4 a = widen(y[v]), b = widen(z[v]);
+        float4 o;
+        o.x = fmaf(step, a.x - b.x, x[v].x);
+        o.y = fmaf(step, a.y - b.y, x[v].y);
+        o.z = fmaf(step, a.z - b.z, x[v].z);
+        o.w = fmaf(step, a.w - b.w, x[v].w);
+        *reinterpret_cast<float4 *>(p.pool + (int64_t)orow * p.n_pad + j0) = o;
+        const float dd[4] = {o.x - t4[v].x, o.y - t4[v].y, o.z - t4[v].z, o.w - t4[v].w};
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          if (j0 + q < p.n_train)
+            str += dd[q] * dd[q];
+          else if (j0 + q < p.n_cases)
+            ste += dd[q] * dd[q];
+        }
+      }
+      const float2 t = subblock_sum(str, ste);
+      if (lane == 0) sum[k][v][warp] = t;
+    }
+#pragma unroll
+    for (int v = 0; v < 2; ++v) {
+      x[v] = x2[v];
+      y[v] = y2[v];
+      z[v] = z2[v];
+    }
+  }
+}
+
 // Chunk partials of one stream item from its sub-block totals (after a
 // barrier that follows stream_item).
 template <int VEC, int OPB>
