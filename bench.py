@@ -12,7 +12,7 @@ test cases), whole job (all ranks).  Under torchrun every rank runs an
 independent replica (its own run index) of the same workload: weak scaling,
 no collective on the data path.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload mid]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload large]
   python bench.py --impl reference ...   # the CPU oracle timed on the host
 """
 from __future__ import annotations
@@ -36,7 +36,7 @@ import workloads as W  # noqa: E402
 
 METRIC = "semantic updates/s (pop·n·gens/s) and % of HBM peak, vs plain FP32 at stated err"
 UNIT = "semantic updates/s"
-PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "persist_kernel_mid.txt")
+PROFILE_DIR = os.path.join(ROOT, "profiles")
 GEN_KERNEL_SRC = [os.path.join(ROOT, "paper_2106_04034_gb300", "csrc", f)
                   for f in ("k_persist.cu", "k_generation.cu", "stream.cuh", "common.cuh")]
 
@@ -82,17 +82,24 @@ def alu_peak_tops():
     return 152 * 128 * mhz * 1e6 / 1e12
 
 
+def kernel_source_hash() -> str:
+    """Hash of the generation kernels' sources, recorded in ncu summaries."""
+    h = hashlib.sha256()
+    for f in GEN_KERNEL_SRC:
+        h.update(open(f, "rb").read())
+    return h.hexdigest()[:16]
+
+
 def profiled_traffic(workload_name: str):
     """DRAM bytes per generation of the generation kernel from the committed
-    ncu summary, if it was taken on this workload with the current kernel
-    sources (else None)."""
+    ncu summary of this workload (profiles/persist_kernel_<workload>.txt), if
+    it was taken with the current kernel sources (else None).  Summaries of a
+    smaller capture state the traffic scaled to the workload's full size."""
     try:
-        h = hashlib.sha256()
-        for f in GEN_KERNEL_SRC:
-            h.update(open(f, "rb").read())
-        src = h.hexdigest()[:16]
+        src = kernel_source_hash()
+        short = workload_name.split(":")[0].strip().replace("-", "_")
         kv = {}
-        for line in open(PROFILE_SUMMARY):
+        for line in open(os.path.join(PROFILE_DIR, f"persist_kernel_{short}.txt")):
             if ":" in line and not line.startswith("#"):
                 k, v = line.split(":", 1)
                 kv[k.strip()] = v.strip()
@@ -539,16 +546,46 @@ def run_batched(args, rank, world, local_rank):
     return line, ws
 
 
-def oracle_run(w: W.Workload):
+# The oracle keeps every semantic row of a run in float64 host memory; the
+# large workloads (1.25M cases: about 25 GB) are sampled by their cases.
+ORACLE_MAX_CASES = 100_000
+ORACLE_CASE_FRACTION = 64
+
+
+def oracle_sample(w: W.Workload, data=None):
+    """(data, note) for the oracle on workload w: every case when the
+    workload has at most ORACLE_MAX_CASES, else a seeded subset of
+    1/ORACLE_CASE_FRACTION of its training and of its test cases (fitness
+    cases are independent columns of every step but the RMSE sums, so the
+    per-update work is that of the full workload)."""
+    if data is None:
+        data = W.make_data(w)
+    n = int(data[1].shape[0] + data[3].shape[0])
+    if n <= ORACLE_MAX_CASES:
+        return data, (f"full n_cases={n}" if n == w.n_cases else f"{n} sampled cases")
+    rng = np.random.default_rng([w.seed, w.wid, w.run, ORACLE_CASE_FRACTION])
+    itr = np.sort(rng.choice(w.n_train, max(1, w.n_train // ORACLE_CASE_FRACTION), replace=False))
+    ite = np.sort(rng.choice(w.n_test, w.n_test // ORACLE_CASE_FRACTION, replace=False)) \
+        if w.n_test else np.zeros(0, np.int64)
+    sub = (np.ascontiguousarray(data[0][itr]), np.ascontiguousarray(data[1][itr]),
+           np.ascontiguousarray(data[2][ite]), np.ascontiguousarray(data[3][ite]))
+    return sub, (f"seeded 1/{ORACLE_CASE_FRACTION} case subset: {len(itr)} + {len(ite)} of "
+                 f"{w.n_train} + {w.n_test} cases")
+
+
+def oracle_run(w: W.Workload, data=None):
     """The float64 oracle initialised on workload w, or on a sample of it:
-    where the oracle's initialisation would take many minutes (long linear
-    genomes) every case is kept but at most 128 programs per pool.  Returns
-    (oracle, the workload it runs, a note on the sample)."""
+    the cases of large workloads are sampled (oracle_sample); where the
+    oracle's initialisation would take many minutes (long linear genomes)
+    every case is kept but at most 128 programs per pool.  Returns (oracle,
+    the workload it runs, the number of cases it holds, a note on the
+    sample)."""
     from oracle import gsgp as og
     full_m = w.pop_size
     big = w.init_mode == 1 and w.pop_size * w.n_cases * w.max_genes > 2e10
     if big:
         w = w.replace(pop_size=min(w.pop_size, 128), n_random_trees=min(w.n_random_trees, 128))
+    sub, note = oracle_sample(w, data)
     p = og.Params(seed=w.seed, run=w.run, pop_size=w.pop_size,
                   n_random_trees=w.n_random_trees, pop_min_depth=w.pop_min_depth,
                   pop_max_depth=w.pop_max_depth, rt_min_depth=w.rt_min_depth,
@@ -556,28 +593,99 @@ def oracle_run(w: W.Workload):
                   const_lo=w.const_lo, const_hi=w.const_hi, protect_eps=w.protect_eps,
                   sigma_bf16=w.sigma_bf16, init_mode=w.init_mode, max_genes=w.max_genes,
                   p_crossover=w.p_crossover)
-    o = og.GSGP(p, *W.make_data(w))
+    o = og.GSGP(p, *sub)
     o.init()
-    return o, w, (f", m and r cut from {full_m} to {w.pop_size}" if big else "")
+    n = int(sub[1].shape[0] + sub[3].shape[0])
+    if big:
+        note += f", m and r cut from {full_m} to {w.pop_size}"
+    return o, w, n, note
 
 
-def cpu_baseline(w: W.Workload, target_s: float = 12.0, max_gens: int = 200):
-    """The float64 oracle, as it stands, on the host cores: generations of the
-    same workload until about target_s seconds of evolution were timed.  On
-    workloads whose initialisation would take the oracle many minutes the
-    sample keeps every case but at most 128 programs per pool."""
-    o, w, shrunk = oracle_run(w)
+def _oracle_worker(w, sub, target_s, barrier, out):
+    """One all-core leg process: an independent oracle run (its own run
+    index) on the sampled cases, timed for about target_s seconds after
+    every process has finished its initialisation."""
+    o, w, n, _ = oracle_run(w, sub)
+    barrier.wait()
+    t0 = time.perf_counter()
+    gens = 0
+    while (time.perf_counter() - t0) < target_s:
+        o.generation()
+        gens += 1
+    out.put((w.pop_size * n * gens, t0, time.perf_counter()))
+
+
+def cpu_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def cpu_model():
+    try:
+        for line in open("/proc/cpuinfo"):
+            k, _, v = line.partition(":")
+            if k.strip() in ("model name", "CPU part", "Model"):
+                return v.strip()
+    except Exception:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+def cpu_baseline(w: W.Workload, target_s: float = 10.0, max_gens: int = 200):
+    """The float64 oracle, as it stands, on the host cores: (1) one process,
+    generations of the workload (cases sampled where it is large) until
+    about target_s seconds were timed; (2) every host core: one independent
+    oracle run per core (its own run index, one numpy thread each) on the
+    same sampled cases, timed together for about target_s seconds.  value is
+    the all-core rate; the single-thread rate is reported beside it."""
+    import multiprocessing as mp
+    data = W.make_data(w)
+    o, wo, n, note = oracle_run(w, data)
     t0 = time.perf_counter()
     gens = 0
     while gens < max_gens and (time.perf_counter() - t0) < target_s:
         o.generation()
         gens += 1
     dt = time.perf_counter() - t0
-    return {"value": w.pop_size * w.n_cases * gens / dt, "unit": UNIT, "cores": 1,
-            "kind": "oracle",
-            "sample": f"{gens} generations of the {w.name.split(':')[0]} workload "
-                      f"(full n_cases={w.n_cases}{shrunk}) after an untimed init; "
-                      f"float64 numpy, single thread, {os.cpu_count()} host cores present"}
+    single = wo.pop_size * n * gens / dt
+    del o
+    sub, _ = oracle_sample(w, data)
+    del data
+    cores = cpu_cores()
+    env_keep = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS",
+                                               "MKL_NUM_THREADS")}
+    for k in env_keep:
+        os.environ[k] = "1"
+    ctx = mp.get_context("spawn")   # never fork a process that has used the GPU
+    barrier = ctx.Barrier(cores)
+    out = ctx.Queue()
+    procs = [ctx.Process(target=_oracle_worker,
+                         args=(w.replace(run=w.run + 1 + k), sub, target_s, barrier, out))
+             for k in range(cores)]
+    for pr in procs:
+        pr.start()
+    res = [out.get() for _ in procs]
+    for pr in procs:
+        pr.join()
+    for k, v in env_keep.items():
+        if v is None:
+            os.environ.pop(k, None)
+        else:
+            os.environ[k] = v
+    upd = sum(r[0] for r in res)
+    span = max(r[2] for r in res) - min(r[1] for r in res)
+    allcore = upd / span
+    return {"value": allcore, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{w.name.split(':')[0]} workload, {note}, m={wo.pop_size}; float64 numpy; "
+                      f"all-core leg: {cores} processes, one independent oracle run each (own "
+                      f"run index, one numpy thread), timed together for ~{target_s:.0f} s "
+                      f"after an untimed init; CPU: {cpu_model()}",
+            "single_thread": {"value": single, "unit": UNIT, "cores": 1,
+                              "sample": f"{gens} generations in one process after an untimed "
+                                        f"init"}}
 
 
 def run_reference(args, rank):
@@ -587,7 +695,7 @@ def run_reference(args, rank):
         w = min(W.batched_runs(args.batch_runs), key=lambda x: x.pop_size * x.n_cases)
     else:
         w = resolve_workload(args)
-    o, w, shrunk = oracle_run(w)
+    o, w, n, note = oracle_run(w)
     gens_per_step = max(1, int(args.ref_gens_per_step))
     for _ in range(args.warmup):
         for _ in range(gens_per_step):
@@ -598,17 +706,17 @@ def run_reference(args, rank):
             o.generation()
     dt = time.perf_counter() - t0
     gens = gens_per_step * args.steps
-    value = w.pop_size * w.n_cases * gens / dt
+    value = w.pop_size * n * gens / dt
     sample = (f"{gens_per_step} oracle generations per step of the {w.name.split(':')[0]} "
-              f"workload (full n_cases={w.n_cases}, m={w.pop_size}{shrunk}), float64 numpy, "
-              f"single thread")
+              f"workload ({note}, m={w.pop_size}), float64 numpy, one process; the rate "
+              f"counts offspring x cases x generations actually computed")
     return {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "impl": "reference",
         "config": {"workload": w.name, "pop_size": w.pop_size, "n_cases": w.n_cases,
-                   "generations_per_step": gens_per_step},
+                   "oracle_cases": n, "generations_per_step": gens_per_step},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -621,7 +729,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="mid", choices=sorted(W.WORKLOADS) + ["batched"])
+    ap.add_argument("--workload", default="large", choices=sorted(W.WORKLOADS) + ["batched"])
     ap.add_argument("--generations", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-gens-per-step", type=int, default=3)

@@ -469,15 +469,24 @@ void gsgp_batch_destroy(gsgp_batch *batch);
  * library routine.  Limit: m * ceil((n_train + n_test) / 1024) <= 131072 and
  * m, ceil(n / 1024) <= 65535; larger sizes return GSGP_E_INVALID.
  *
- * The first call on a device looks up the scratch array's device address
- * (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture.  Every call shares the one scratch array: calls
- * that overlap on the GPU (for example on two streams) race and must be
- * serialised by the caller.  Nothing in the scratch needs clearing between
- * calls: each call writes every partial it reads.
+ * offspring must not overlap parents, sigma_r or target: the call reads those
+ * while it writes the offspring, so an in-place call (offspring == parents)
+ * would race; an input that starts inside the m offspring rows is refused.
+ *
+ * The first call on a device, and the first call in a context the library has
+ * not seen on that device (for example after cudaDeviceReset), looks up the
+ * scratch array's device address (cudaGetSymbolAddress) with that device
+ * current and caches it per context; make that first call before any stream
+ * capture.  Every call shares the one scratch array: calls that overlap on
+ * the GPU (for example on two streams) race and must be serialised by the
+ * caller.  Nothing in the scratch needs clearing between calls: each call
+ * writes every partial it reads.  The offspring and RMSE equal bit for bit
+ * what gsgp_evolve computes for the same draws (same per-case arithmetic,
+ * same summation order).
  *
  * err_msg (nullable, err_cap bytes) receives a message on failure.
- * Errors: GSGP_E_INVALID (sizes, NULL or misaligned pointers), GSGP_E_CUDA. */
+ * Errors: GSGP_E_INVALID (sizes, NULL, misaligned or overlapping pointers),
+ * GSGP_E_CUDA. */
 gsgp_status gsgp_mutate_noalloc(const float *parents, const float *sigma_r, int64_t ld,
                                 const float *target, int64_t n_train, int64_t n_test,
                                 const int32_t *parent, const int32_t *rt1, const int32_t *rt2,

@@ -504,20 +504,83 @@ def rng_words(seed: int, run: int, gen_or_purpose: int, individual: int, n_words
     return out
 
 
+def check_noalloc_args(parents, sigma_r, target, n_train, n_test, parent, rt1, rt2, ms,
+                       offspring, rmse_train, rmse_test, device) -> int:
+    """Validate the tensors of gsgp_mutate_noalloc before any launch: every
+    tensor on ``device`` and contiguous; parents / sigma_r / offspring float32
+    matrices with the common row stride ld = parents.shape[1] >= n_train +
+    n_test; offspring with at least m rows and not the same memory as parents,
+    sigma_r or target (the call reads those while it writes offspring);
+    target float32 with at least ld elements; parent / rt1 / rt2 int32 and ms
+    float32 with m = parent.numel() elements each; rmse outputs float64 with
+    at least m elements.  The library itself checks sizes, alignment and the
+    scratch limit but cannot see dtypes or buffer extents.  Returns m; raises
+    GsgpError(E_INVALID) on the first violation."""
+    import torch
+
+    def bad(text):
+        raise GsgpError(E_INVALID, f"mutate_noalloc: {text}")
+
+    named = (("parents", parents), ("sigma_r", sigma_r), ("target", target), ("parent", parent),
+             ("rt1", rt1), ("rt2", rt2), ("ms", ms), ("offspring", offspring),
+             ("rmse_train", rmse_train), ("rmse_test", rmse_test))
+    for name, t in named:
+        if not isinstance(t, torch.Tensor):
+            bad(f"{name} must be a torch tensor")
+        if t.device != device:
+            bad(f"{name} is on {t.device}, expected {device}")
+        if not t.is_contiguous():
+            bad(f"{name} must be contiguous")
+    for name, t in (("parents", parents), ("sigma_r", sigma_r), ("offspring", offspring)):
+        if t.dtype != torch.float32 or t.dim() != 2:
+            bad(f"{name} must be a float32 matrix")
+    ld = int(parents.shape[1])
+    if ld < int(n_train) + int(n_test):
+        bad("the row stride parents.shape[1] is below n_train + n_test")
+    for name, t in (("sigma_r", sigma_r), ("offspring", offspring)):
+        if int(t.shape[1]) != ld:
+            bad(f"{name} must have parents.shape[1] = {ld} columns")
+    if target.dtype != torch.float32 or target.numel() < ld:
+        bad(f"target must be float32 with at least {ld} elements")
+    m = int(parent.numel())
+    for name, t in (("parent", parent), ("rt1", rt1), ("rt2", rt2)):
+        if t.dtype != torch.int32 or t.numel() != m:
+            bad(f"{name} must be int32 with m = {m} elements")
+    if ms.dtype != torch.float32 or ms.numel() != m:
+        bad(f"ms must be float32 with m = {m} elements")
+    if int(offspring.shape[0]) < m:
+        bad(f"offspring must have at least m = {m} rows")
+    for name, t in (("rmse_train", rmse_train), ("rmse_test", rmse_test)):
+        if t.dtype != torch.float64 or t.numel() < m:
+            bad(f"{name} must be float64 with at least m = {m} elements")
+    o0 = offspring.data_ptr()
+    o1 = o0 + offspring.numel() * 4
+    for name, t in (("parents", parents), ("sigma_r", sigma_r), ("target", target)):
+        a0 = t.data_ptr()
+        a1 = a0 + t.numel() * t.element_size()
+        if a0 < o1 and o0 < a1:
+            bad(f"offspring overlaps {name}")
+    return m
+
+
 def mutate_noalloc(parents, sigma_r, target, n_train, n_test, parent, rt1, rt2, ms, offspring,
                    rmse_train, rmse_test, stream=None):
     """gsgp_mutate_noalloc on torch CUDA tensors (row-major, common row
     stride = parents.shape[1]); queued on `stream` (default: torch's current
-    stream).  Raises GsgpError with the library's message on failure."""
+    stream).  The tensors are validated first (check_noalloc_args); raises
+    GsgpError with the library's message on failure."""
+    import torch
     lib = load_library()
+    device = torch.device("cuda", torch.cuda.current_device())
+    m = check_noalloc_args(parents, sigma_r, target, n_train, n_test, parent, rt1, rt2, ms,
+                           offspring, rmse_train, rmse_test, device)
     if stream is None:
-        import torch
         stream = torch.cuda.current_stream()
     s = stream if isinstance(stream, int) else stream.cuda_stream
     msg = C.create_string_buffer(256)
     st = lib.gsgp_mutate_noalloc(_ptr(parents), _ptr(sigma_r), int(parents.shape[1]),
                                  _ptr(target), n_train, n_test, _ptr(parent), _ptr(rt1),
-                                 _ptr(rt2), _ptr(ms), int(parent.shape[0]), _ptr(offspring),
+                                 _ptr(rt2), _ptr(ms), m, _ptr(offspring),
                                  _ptr(rmse_train), _ptr(rmse_test), s, msg, 256)
     if st != OK:
         raise GsgpError(st, msg.value.decode())

@@ -11,8 +11,11 @@
 // file-scope device array below instead of a cudaMalloc'd buffer.
 //
 // The per-chunk summation order is the library's canonical one (chunk_total)
-// and chunks are added in the same fixed lane-strided order, so the results
-// equal the ones the library computes for the same offspring.
+// and chunks are added in the same fixed lane-strided order, so the offspring
+// and their RMSE equal, bit for bit, the ones the library computes for the
+// same draws.
+#include <cuda.h>
+
 #include <mutex>
 
 #include "gsgp.h"
@@ -72,11 +75,50 @@ __global__ void __launch_bounds__(256) noalloc_rmse_kernel(const GenParams p, co
   }
 }
 
-// Device address of the scratch array, looked up once per device with that
-// device current (the host-side symbol is only a stand-in for it).
+// Device address of the scratch array.  The host-side symbol is only a
+// stand-in for it, so the address is looked up with cudaGetSymbolAddress
+// once per device with that device current, and cached.  The address
+// belongs to the module loaded into one CUDA context; after a
+// cudaDeviceReset (or under another context) the same device has a new
+// module and a new address.  The cache is therefore keyed by the current
+// context's unique id (cuCtxGetCurrent + cuCtxGetId, reached through the
+// runtime's driver entry points, so the library needs no link against
+// libcuda), and a context it has not seen triggers a fresh lookup.
 constexpr int kMaxDevices = 64;
 static std::mutex g_noalloc_mu;
-static double2 *g_noalloc_addr[kMaxDevices];
+struct ScratchEntry {
+  unsigned long long ctx_id;   // 0: empty
+  double2 *addr;
+};
+static ScratchEntry g_noalloc_addr[kMaxDevices];
+
+typedef CUresult (*PfnCtxGetCurrent)(CUcontext *);
+typedef CUresult (*PfnCtxGetId)(CUcontext, unsigned long long *);
+
+// Unique id of the calling thread's current context (0 if none is current
+// yet); resolves the two driver entry points on first use.
+static cudaError_t current_ctx_id(unsigned long long *id) {
+  static PfnCtxGetCurrent get_current = nullptr;
+  static PfnCtxGetId get_id = nullptr;
+  if (!get_current || !get_id) {
+    void *f1 = nullptr, *f2 = nullptr;
+    cudaDriverEntryPointQueryResult q1, q2;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000,
+                                                     cudaEnableDefault, &q1);
+    if (e != cudaSuccess) return e;
+    e = cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2);
+    if (e != cudaSuccess) return e;
+    if (q1 != cudaDriverEntryPointSuccess || q2 != cudaDriverEntryPointSuccess || !f1 || !f2)
+      return cudaErrorSymbolNotFound;
+    get_current = reinterpret_cast<PfnCtxGetCurrent>(f1);
+    get_id = reinterpret_cast<PfnCtxGetId>(f2);
+  }
+  CUcontext ctx = nullptr;
+  if (get_current(&ctx) != CUDA_SUCCESS) return cudaErrorContextIsDestroyed;
+  *id = 0;
+  if (ctx && get_id(ctx, id) != CUDA_SUCCESS) return cudaErrorContextIsDestroyed;
+  return cudaSuccess;
+}
 
 static cudaError_t noalloc_scratch(double2 **out) {
   int dev = 0;
@@ -84,13 +126,22 @@ static cudaError_t noalloc_scratch(double2 **out) {
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
   std::lock_guard<std::mutex> lock(g_noalloc_mu);
-  if (!g_noalloc_addr[dev]) {
-    void *ptr = nullptr;
-    e = cudaGetSymbolAddress(&ptr, g_noalloc_partials);
-    if (e != cudaSuccess) return e;
-    g_noalloc_addr[dev] = static_cast<double2 *>(ptr);
+  unsigned long long id = 0;
+  e = current_ctx_id(&id);
+  if (e != cudaSuccess) return e;
+  if (id != 0 && g_noalloc_addr[dev].ctx_id == id) {
+    *out = g_noalloc_addr[dev].addr;
+    return cudaSuccess;
   }
-  *out = g_noalloc_addr[dev];
+  // set-up on this device and context: the lookup also makes the device's
+  // primary context current if no context was yet
+  void *ptr = nullptr;
+  e = cudaGetSymbolAddress(&ptr, g_noalloc_partials);
+  if (e != cudaSuccess) return e;
+  e = current_ctx_id(&id);
+  if (e != cudaSuccess) return e;
+  g_noalloc_addr[dev] = ScratchEntry{id, static_cast<double2 *>(ptr)};
+  *out = static_cast<double2 *>(ptr);
   return cudaSuccess;
 }
 
@@ -128,6 +179,13 @@ extern "C" gsgp_status gsgp_mutate_noalloc(const float *parents, const float *si
                           (uintptr_t)offspring;
   if (align % 16 != 0)
     return noalloc_fail(err_msg, err_cap, GSGP_E_INVALID, "row buffers must be 16-byte aligned");
+  // offspring is written while parents, sigma_r and target are read: an
+  // input that starts inside the offspring rows (an in-place call) races
+  const uintptr_t o0 = (uintptr_t)offspring, o1 = o0 + (uintptr_t)m * (uintptr_t)ld * 4u;
+  for (const void *in : {(const void *)parents, (const void *)sigma_r, (const void *)target})
+    if ((uintptr_t)in >= o0 && (uintptr_t)in < o1)
+      return noalloc_fail(err_msg, err_cap, GSGP_E_INVALID,
+                          "offspring must not overlap parents, sigma_r or target");
   const int64_t chunks = (n + 1023) / 1024;
   if ((int64_t)m * chunks > kNoAllocMaxPartials)
     return noalloc_fail(err_msg, err_cap, GSGP_E_INVALID,

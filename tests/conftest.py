@@ -32,3 +32,18 @@ def read_golden(name: str):
 @pytest.fixture
 def golden():
     return read_golden
+
+
+def pytest_terminal_summary(terminalreporter):
+    """Shares of the bounded semantic comparisons of the session: cases that
+    passed only because they lie within twice the oracle's float32 running
+    error bound, and cases whose bound is infinite (excused)."""
+    mod = sys.modules.get("gpu_util")
+    shares = getattr(mod, "SHARES", None) if mod is not None else None
+    if not shares:
+        return
+    terminalreporter.write_line("")
+    terminalreporter.write_line("bounded semantic comparisons (outside 1e-4 (1 + |v|) of float64):")
+    for label, n, b, a in shares:
+        terminalreporter.write_line(
+            f"  {label}: {n} cases, within 2x the float32 bound {b:.2e}, infinite bound {a:.2e}")

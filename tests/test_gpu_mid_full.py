@@ -36,11 +36,11 @@ def test_mid_full_size():
     S_T0 = run.semantics(pkg.POOL_POPULATION)
     S_R = run.semantics(pkg.POOL_RANDOM)
     vT, eT = oracle_semantics_with_bounds(ref.P, ref.X, p.protect_eps)
-    ok, _, amb = semantics_close(S_T0, vT, eT)
-    assert ok.all() and amb < 1e-3
+    ok, _, _ = semantics_close(S_T0, vT, eT, label="mid full size, population")
+    assert ok.all()
     del vT, eT
     vR, eR = oracle_semantics_with_bounds(ref.R, ref.X, p.protect_eps, logistic=True)
-    ok, _, _ = semantics_close(S_R, vR, eR)
+    ok, _, _ = semantics_close(S_R, vR, eR, label="mid full size, random trees")
     assert ok.all()
     del vR, eR
     ref.set_state(S_T0, S_R)

@@ -5,6 +5,8 @@ generation step (gsgp_evolve) on two calls in a row.
 
 This file is collected last so that a run stopping at the first failure has
 already run every other test."""
+import ctypes
+
 import numpy as np
 import pytest
 
@@ -61,10 +63,38 @@ def test_noalloc_matches_evolve_on_two_calls_in_a_row():
         if call == 1:   # the first call may load the kernels' module
             assert torch.cuda.mem_get_info()[0] == free_before
         got = off[:, :n].cpu().numpy()
+        # the same per-case arithmetic and summation order as gsgp_evolve:
+        # equal values (the elite's copy of its parent included), and within
+        # the tests' tolerances in any case
         assert np.all(np.abs(got - cur) <= SEM_RTOL * (1 + np.abs(cur)))
         assert np.allclose(rtr.cpu().numpy(), f_tr, rtol=RMSE_RTOL, atol=0)
         assert np.allclose(rte.cpu().numpy(), f_te, rtol=RMSE_RTOL, atol=0)
+        assert np.array_equal(got, cur, equal_nan=True)
+        assert np.array_equal(rtr.cpu().numpy(), f_tr)
+        assert np.array_equal(rte.cpu().numpy(), f_te)
     run.close()
+
+
+def test_noalloc_refuses_an_in_place_call():
+    """offspring == parents would race (rows are read while others are
+    written); the library refuses it before any launch."""
+    torch.cuda.set_device(0)
+    m, n = 4, 2048
+    rows = torch.zeros((m, n), dtype=torch.float32, device="cuda")
+    sig = torch.zeros((2, n), dtype=torch.float32, device="cuda")
+    target = torch.zeros(n, dtype=torch.float32, device="cuda")
+    i32 = torch.zeros(m, dtype=torch.int32, device="cuda")
+    f32 = torch.zeros(m, dtype=torch.float32, device="cuda")
+    r = torch.zeros(m, dtype=torch.float64, device="cuda")
+    # straight through the C ABI: the binding would refuse it first
+    lib = pkg.load_library()
+    msg = ctypes.create_string_buffer(256)
+    ptr = [t.data_ptr() for t in (rows, sig, target, i32, f32, r)]
+    st = lib.gsgp_mutate_noalloc(ptr[0], ptr[1], n, ptr[2], n - 48, 48, ptr[3], ptr[3], ptr[3],
+                                 ptr[4], m, ptr[0], ptr[5], ptr[5],
+                                 torch.cuda.current_stream().cuda_stream, msg, 256)
+    torch.cuda.synchronize()
+    assert st == E_INVALID and b"overlap" in msg.value
 
 
 def test_noalloc_rejects_sizes_beyond_its_scratch():
@@ -75,7 +105,7 @@ def test_noalloc_rejects_sizes_beyond_its_scratch():
     target = torch.zeros(ld, dtype=torch.float32, device="cuda")
     i32 = torch.zeros(m, dtype=torch.int32, device="cuda")
     f32 = torch.zeros(m, dtype=torch.float32, device="cuda")
-    out = torch.zeros((1, 4), dtype=torch.float32, device="cuda")
+    out = torch.zeros((m, ld), dtype=torch.float32, device="cuda")
     r = torch.zeros(m, dtype=torch.float64, device="cuda")
     with pytest.raises(pkg.GsgpError) as e:
         mutate_noalloc(rows, rows, target, n - 100, 100, i32, i32, i32, f32, out, r, r)
