@@ -177,6 +177,20 @@ gsgp_status gsgp_init(gsgp_ctx *ctx);
  * GSGP_E_TIMEOUT: a bounded wait of the persistent generation kernel gave up
  * (never expected; the run must be restarted with gsgp_init). */
 
+/* Test hook of the GSGP_E_TIMEOUT path (the paper has no counterpart).  Arms,
+ * for the next launch of the persistent generation kernel only (the next
+ * gsgp_evolve on that path, after its shape was chosen), a bound of
+ * spin_limit naps (1024 .. 2^24; the default bound is 2^24, about a second)
+ * on every grid-barrier wait, and starts that launch's barrier arrival
+ * counter one arrival short, as if one CTA never arrived at the first
+ * barrier.  Every CTA's bounded wait there runs out, the sticky error word is
+ * set, every CTA leaves the kernel (none passes the barrier), later launches
+ * return at once, and the next call that synchronises (gsgp_evolve with a
+ * log, gsgp_best_trace, ...) returns GSGP_E_TIMEOUT; gsgp_init clears it and
+ * the context is usable again.  No kernel faults, traps or waits without
+ * bound.  Errors: GSGP_E_INVALID (spin_limit out of range). */
+gsgp_status gsgp_arm_barrier_fault(gsgp_ctx *ctx, uint32_t spin_limit);
+
 /* Run `generations` generations of the loop of Algorithm 1 (GSM, fitness of
  * the offspring, survival with elitism), continuing from the current one.
  * best_train_rmse / best_test_rmse (nullable HOST arrays of `generations`

@@ -112,6 +112,7 @@ _SIGS = {
     "gsgp_get_fitness": (C.c_int, [P, P, P]),
     "gsgp_get_trace": (C.c_int, [P, C.c_int32, C.c_int32, P, P, P, P]),
     "gsgp_set_evolve_shape": (C.c_int, [P, C.c_int32, C.c_int32, C.c_int32]),
+    "gsgp_arm_barrier_fault": (C.c_int, [P, C.c_uint32]),
     "gsgp_set_kernel_timing": (C.c_int, [P, C.c_int32]),
     "gsgp_kernel_times": (C.c_int, [P, P, C.c_int32, P]),
     "gsgp_init_kernel_times": (C.c_int, [P, P]),
@@ -377,6 +378,10 @@ class Run:
 
     def set_evolve_shape(self, path: int, vec: int = 0, opb: int = 0):
         self._check(self.lib.gsgp_set_evolve_shape(self.ctx, path, vec, opb))
+
+    def arm_barrier_fault(self, spin_limit: int):
+        """Test hook of the timeout path (gsgp_arm_barrier_fault)."""
+        self._check(self.lib.gsgp_arm_barrier_fault(self.ctx, spin_limit))
 
     def set_kernel_timing(self, enabled: bool):
         self._check(self.lib.gsgp_set_kernel_timing(self.ctx, int(enabled)))

@@ -721,9 +721,18 @@ static gsgp_status ensure_cta_arrays(gsgp_ctx *c, int grid) {
 
 static gsgp_status launch_persist_chunk(gsgp_ctx *c, int G) {
   const GenParams p = gen_params(c);
-  PersistArgs x{c->gs, c->cta_min, c->cta_max, G};
+  PersistArgs x{c->gs, c->cta_min, c->cta_max, G, kSpinLimitDefault};
   CK(cudaMemsetAsync(&c->gs->count, 0, grid_sync_bytes(c->grid) - offsetof(GridSync, count),
                      c->stream));
+  if (c->fault_spin_limit) {
+    // the timeout test (one launch only): the arrival counter starts one
+    // arrival short (2^32 - 1: the first arrival wraps it to 0), so after
+    // every CTA has arrived at the first barrier the count is grid - 1 and
+    // every wait runs out after fault_spin_limit naps; no CTA passes it
+    x.spin_limit = c->fault_spin_limit;
+    CK(cudaMemsetAsync(&c->gs->count, 0xff, sizeof(unsigned), c->stream));
+    c->fault_spin_limit = 0;
+  }
   LAUNCH(1, launch_persist(p, x, c->cfg.sigma_dtype == GSGP_SIGMA_BF16, c->shape, c->grid,
                            c->stream));
   return GSGP_OK;
@@ -1007,6 +1016,15 @@ extern "C" gsgp_status gsgp_evolve(gsgp_ctx *c, int32_t generations, double *bes
       if (best_test) best_test[k] = h[k].y;
     }
   }
+  return GSGP_OK;
+  API_END(c)
+}
+
+extern "C" gsgp_status gsgp_arm_barrier_fault(gsgp_ctx *c, uint32_t spin_limit) {
+  API_GUARD(c)
+  if (spin_limit < 1024 || spin_limit > kSpinLimitDefault)
+    return fail(c, GSGP_E_INVALID, "spin_limit must be in [1024, 2^24]");
+  c->fault_spin_limit = spin_limit;
   return GSGP_OK;
   API_END(c)
 }

@@ -40,6 +40,8 @@ struct gsgp_ctx {
   bool shape_ready = false;
   GridSync *gs = nullptr;
   ulonglong2 *cta_min = nullptr, *cta_max = nullptr;
+  // armed by gsgp_arm_barrier_fault for the next persistent launch only
+  unsigned fault_spin_limit = 0;   // 0: not armed
   int cta_cap = 0;
   int *bk_perm = nullptr;    // state snapshot used while autotuning
   double *bk_fit = nullptr, *bk_fit_te = nullptr;

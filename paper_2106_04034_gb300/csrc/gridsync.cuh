@@ -6,7 +6,7 @@
 
 namespace gsgp {
 
-constexpr unsigned kSpinLimit = 1u << 24;   // ~1 s of 32-64 ns naps
+constexpr unsigned kSpinLimit = kSpinLimitDefault;
 
 __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p) {
   unsigned v;
@@ -21,12 +21,13 @@ __device__ __forceinline__ int ld_relaxed_s32(const int *p) {
 }
 
 // Bounded wait until *p >= target; false (and the sticky error word set)
-// when the bound is hit or another CTA already gave up.
-__device__ __forceinline__ bool wait_at_least(const unsigned *p, unsigned target, GridSync *gs) {
+// when `limit` naps have passed or another CTA already gave up.
+__device__ __forceinline__ bool wait_at_least(const unsigned *p, unsigned target, GridSync *gs,
+                                              unsigned limit = kSpinLimit) {
   unsigned spins = 0;
   while (ld_acquire_u32(p) < target) {
     if (ld_relaxed_s32(&gs->err) != 0) return false;
-    if (++spins > kSpinLimit) {
+    if (++spins > limit) {
       atomicExch(&gs->err, 1);
       return false;
     }
@@ -47,6 +48,23 @@ __device__ __forceinline__ bool grid_sync(GridSync *gs, unsigned &epoch, int *s_
     __threadfence();
     atomicAdd(&gs->count, 1u);
     const bool ok = wait_at_least(&gs->count, epoch * gridDim.x, gs);
+    __threadfence();
+    *s_ok = ok;
+  }
+  __syncthreads();
+  return *s_ok != 0;
+}
+
+// grid_sync of the persistent kernels with the launch's wait bound (read by
+// thread 0 only, from the kernel's parameter block).
+__device__ __forceinline__ bool grid_sync_args(const PersistArgs &x, unsigned &epoch, int *s_ok) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    ++epoch;
+    __threadfence();
+    atomicAdd(&x.gs->count, 1u);
+    const bool ok = wait_at_least(&x.gs->count, epoch * gridDim.x, x.gs,
+                                  x.spin_limit ? x.spin_limit : kSpinLimit);
     __threadfence();
     *s_ok = ok;
   }

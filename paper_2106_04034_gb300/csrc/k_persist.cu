@@ -280,6 +280,7 @@ __global__ void __launch_bounds__(kGenThreads, 4) persist_kernel(const GenParams
   const int tiles = (int)((p.n_pad + W - 1) / W);
   const int items = tiles * groups;
   unsigned epoch = 0;
+  auto barrier = [&]() { return grid_sync_args(x, epoch, &s_ok); };
 
   if (tid == 0) {
     st.g = __ldcg(&p.state->gen);
@@ -296,7 +297,7 @@ __global__ void __launch_bounds__(kGenThreads, 4) persist_kernel(const GenParams
   for (int it = 0; it < x.G; ++it) {
     // ---------------- S: selection ----------------------------------------
     select_phase<CROSS>(p, st, b, nb);
-    if (!grid_sync(gs, epoch, &s_ok)) return;
+    if (!barrier()) return;
 
     // ---------------- M: mutation stream ----------------------------------
     // CTA b streams items b, b + grid, ... in tile-major order; the grid is
@@ -362,11 +363,11 @@ __global__ void __launch_bounds__(kGenThreads, 4) persist_kernel(const GenParams
         item_partials<VEC, OPB>(p, tile, i0, cnt, s_sum[buf]);
       }
     }
-    if (!grid_sync(gs, epoch, &s_ok)) return;
+    if (!barrier()) return;
 
     // ---------------- F1: offspring RMSE ----------------------------------
     fitness_phase(p, x, st.par, b, nb, s_sse);
-    if (!grid_sync(gs, epoch, &s_ok)) return;
+    if (!barrier()) return;
 
     // ---------------- F2: survival with elitism ---------------------------
     survive_phase(p, x, st, b, nb, it + 1 == x.G, s_min, s_max);
@@ -488,6 +489,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1) persist_tma_kernel(const GenPa
   const SigT *sig = static_cast<const SigT *>(p.sigma_r);
   unsigned epoch = 0;
   unsigned u0 = 0;   // units this CTA has run in earlier generations of the launch
+  auto barrier = [&]() { return grid_sync_args(x, epoch, &s_ok); };
 
   if (tid == 0) {
     for (int k = 0; k < S; ++k) {
@@ -509,7 +511,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1) persist_tma_kernel(const GenPa
 
   for (int it = 0; it < x.G; ++it) {
     select_phase<false>(p, st, b, nb);
-    if (!grid_sync(gs, epoch, &s_ok)) return;
+    if (!barrier()) return;
 
     // ---------------- M: TMA-staged mutation stream -----------------------
     bool ok = true;
@@ -667,10 +669,10 @@ __global__ void __launch_bounds__(kTmaThreads, 1) persist_tma_kernel(const GenPa
       return;
     }
     u0 += (unsigned)nunits;
-    if (!grid_sync(gs, epoch, &s_ok)) return;
+    if (!barrier()) return;
 
     fitness_phase(p, x, st.par, b, nb, s_sse);
-    if (!grid_sync(gs, epoch, &s_ok)) return;
+    if (!barrier()) return;
 
     survive_phase(p, x, st, b, nb, it + 1 == x.G, s_min, s_max);
   }

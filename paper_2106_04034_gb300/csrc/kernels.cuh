@@ -76,11 +76,15 @@ struct GridSync {
   unsigned pad1[kSyncStride - 1];
 };
 inline size_t grid_sync_bytes(int /*grid*/) { return sizeof(GridSync); }
+// Naps (__nanosleep(64) plus one L2 round trip each) a barrier wait may
+// spend before it gives up: about a second.
+constexpr unsigned kSpinLimitDefault = 1u << 24;
 struct PersistArgs {
   GridSync *gs;
   ulonglong2 *cta_min;   // [grid] (fitness key, index) arg-min of each CTA's offspring
   ulonglong2 *cta_max;   // [grid] (fitness key, index) arg-max
   int G;              // generations this launch runs
+  unsigned spin_limit;   // bound of every barrier wait (kSpinLimitDefault)
 };
 bool persist_shape_supported(const GenShape &sh);
 // Co-resident CTAs of the persistent kernel for this shape (0: no cooperative launch).

@@ -191,3 +191,15 @@ def test_checkpoint_needs_a_run(lib):
     assert lib.gsgp_restore(r.ctx, buf, 64) == B.E_STATE
     assert lib.gsgp_restore(None, buf, 64) == B.E_INVALID
     r.close()
+
+
+def test_barrier_fault_hook_checks_its_arguments(lib):
+    """The timeout test hook validates on the host and only arms the next
+    persistent launch (no device work here)."""
+    r = pkg.Run(pop_size=8, n_random_trees=4)
+    assert lib.gsgp_arm_barrier_fault(None, 4096) == B.E_INVALID
+    for bad in (0, 1023, (1 << 24) + 1):
+        assert lib.gsgp_arm_barrier_fault(r.ctx, bad) == B.E_INVALID, bad
+    assert lib.gsgp_arm_barrier_fault(r.ctx, 4096) == B.OK
+    assert lib.gsgp_arm_barrier_fault(r.ctx, 1 << 24) == B.OK
+    r.close()
