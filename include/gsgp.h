@@ -177,6 +177,73 @@ gsgp_status gsgp_init(gsgp_ctx *ctx);
  * GSGP_E_TIMEOUT: a bounded wait of the persistent generation kernel gave up
  * (never expected; the run must be restarted with gsgp_init). */
 
+/* ---- Case sharding -----------------------------------------------------------
+ *
+ * The paper notes that large datasets need the semantic matrix partitioned
+ * (Sec. 2.2, "Fitness computation"); every step of a generation is
+ * independent per fitness case except the squared-error sums of the RMSE.
+ * A problem of n_train_all + n_test_all cases (training cases first, as in
+ * gsgp_load) can therefore be split into K shard contexts, one per GPU or
+ * several on one GPU, each holding a contiguous slice of the cases:
+ *
+ *   shard k holds cases [case0_k, case0_(k+1)); case0_0 = 0; every case0 is
+ *   a multiple of 1024 and every shard but the last holds a multiple of 1024
+ *   cases.  Its gsgp_load gets exactly its slice: the slice's training cases
+ *   (those below n_train_all) as X_train / y_train (possibly none) and its
+ *   test cases as X_test / y_test.
+ *
+ * All shards share one gsgp_config (seed, run, sizes), so they generate the
+ * same programs and draw the same selections and random trees.  Each shard
+ * writes the (train, test) squared-error sum of every individual and every
+ * 1024-case chunk it holds into a partial-sum array of pop_size x chunks
+ * (double pairs, chunk c of the whole problem at column c), with zeros in
+ * the other shards' columns.  Between a step and its completion the caller
+ * replaces every shard's array by the element-wise sum over all shards (an
+ * all-reduce; exact, since each element has one non-zero term).  The
+ * completion then sums the chunks in the library's fixed order, so fitness,
+ * every selection and survival decision, the trace and the semantics equal,
+ * bit for bit, those of one unsharded context over all the cases.
+ *
+ *   gsgp_shard_configure (before gsgp_load) -> gsgp_load (the slice)
+ *   -> gsgp_init -> [exchange] -> gsgp_shard_finish
+ *   -> { gsgp_shard_generation -> [exchange] -> gsgp_shard_finish } * G
+ *
+ * The exchange must be ordered after the preceding call's work on the
+ * context's stream and must complete before the next call's work starts
+ * (e.g. an all-reduce queued on the same stream).  gsgp_evolve, checkpoints
+ * and batches refuse shard contexts; gsgp_best_trace and gsgp_predict work
+ * on any shard (the trace is the same on all). */
+
+/* Make ctx (created, no data loaded yet) shard `case0` of a problem of
+ * n_train_all training and n_test_all test cases.  Errors: GSGP_E_STATE
+ * (data already loaded), GSGP_E_INVALID (case0 not a multiple of 1024 or
+ * not below the case count, n_train_all < 1, n_test_all < 0). */
+gsgp_status gsgp_shard_configure(gsgp_ctx *ctx, int64_t case0, int64_t n_train_all,
+                                 int64_t n_test_all);
+
+/* The device partial-sum array of the pending exchange: *partials receives
+ * a DEVICE pointer to rows x chunks pairs of doubles (row-major, (train,
+ * test) per chunk), owned by the context and valid until its next
+ * gsgp_init; *rows = pop_size, *chunks = 1024-case chunks of the whole
+ * problem.  Each output pointer may be NULL.  Errors: GSGP_E_STATE (not a
+ * shard, or no exchange pending). */
+gsgp_status gsgp_shard_partials(gsgp_ctx *ctx, double **partials, int64_t *rows,
+                                int64_t *chunks);
+
+/* Queue one generation's selection and mutation stream (Algorithm 1: GSM
+ * and the squared errors of the offspring) on the shard's cases and leave
+ * the partial sums for the exchange.  Does not synchronise.  Errors:
+ * GSGP_E_STATE (not a shard, not initialised, or an exchange pending),
+ * GSGP_E_OOM, GSGP_E_CUDA. */
+gsgp_status gsgp_shard_generation(gsgp_ctx *ctx);
+
+/* Complete the pending step from the exchanged partial sums: after
+ * gsgp_init, the initial population's fitness; after gsgp_shard_generation,
+ * the offspring's RMSE and survival with elitism (the generation counts from
+ * here).  Does not synchronise.  Errors: GSGP_E_STATE (not a shard or
+ * nothing pending), GSGP_E_CUDA. */
+gsgp_status gsgp_shard_finish(gsgp_ctx *ctx);
+
 /* Test hook of the GSGP_E_TIMEOUT path (the paper has no counterpart).  Arms,
  * for the next launch of the persistent generation kernel only (the next
  * gsgp_evolve on that path, after its shape was chosen), a bound of

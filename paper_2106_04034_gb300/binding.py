@@ -113,6 +113,11 @@ _SIGS = {
     "gsgp_get_trace": (C.c_int, [P, C.c_int32, C.c_int32, P, P, P, P]),
     "gsgp_set_evolve_shape": (C.c_int, [P, C.c_int32, C.c_int32, C.c_int32]),
     "gsgp_arm_barrier_fault": (C.c_int, [P, C.c_uint32]),
+    "gsgp_shard_configure": (C.c_int, [P, C.c_int64, C.c_int64, C.c_int64]),
+    "gsgp_shard_partials": (C.c_int, [P, C.POINTER(C.c_void_p), C.POINTER(C.c_int64),
+                                      C.POINTER(C.c_int64)]),
+    "gsgp_shard_generation": (C.c_int, [P]),
+    "gsgp_shard_finish": (C.c_int, [P]),
     "gsgp_set_kernel_timing": (C.c_int, [P, C.c_int32]),
     "gsgp_kernel_times": (C.c_int, [P, P, C.c_int32, P]),
     "gsgp_init_kernel_times": (C.c_int, [P, P]),
@@ -202,6 +207,16 @@ class TorchAllocator:
 
         self.alloc_fn = ALLOC_FN(_alloc)
         self.free_fn = FREE_FN(_free)
+
+
+class _DeviceArray:
+    """A device buffer owned by the library, described by the CUDA array
+    interface so that torch can view it without a copy."""
+
+    def __init__(self, ptr: int, shape, typestr: str):
+        self.__cuda_array_interface__ = {"shape": tuple(int(s) for s in shape),
+                                         "typestr": typestr, "data": (int(ptr), False),
+                                         "version": 2}
 
 
 class Run:
@@ -378,6 +393,29 @@ class Run:
 
     def set_evolve_shape(self, path: int, vec: int = 0, opb: int = 0):
         self._check(self.lib.gsgp_set_evolve_shape(self.ctx, path, vec, opb))
+
+    # -- case sharding (gsgp_shard_*) ----------------------------------------
+    def shard_configure(self, case0: int, n_train_all: int, n_test_all: int):
+        """Make this (not yet loaded) run the shard holding the problem's
+        cases from case0 on; load() then gets exactly that slice."""
+        self._check(self.lib.gsgp_shard_configure(self.ctx, case0, n_train_all, n_test_all))
+
+    def shard_partials(self):
+        """The pending exchange's partial sums as a torch CUDA float64 tensor
+        of shape (pop_size, chunks, 2) viewing the library's device array
+        (valid until the next init)."""
+        import torch
+        ptr, rows, chunks = C.c_void_p(), C.c_int64(), C.c_int64()
+        self._check(self.lib.gsgp_shard_partials(self.ctx, C.byref(ptr), C.byref(rows),
+                                                 C.byref(chunks)))
+        return torch.as_tensor(_DeviceArray(ptr.value, (rows.value, chunks.value, 2), "<f8"),
+                               device="cuda")
+
+    def shard_generation(self):
+        self._check(self.lib.gsgp_shard_generation(self.ctx))
+
+    def shard_finish(self):
+        self._check(self.lib.gsgp_shard_finish(self.ctx))
 
     def arm_barrier_fault(self, spin_limit: int):
         """Test hook of the timeout path (gsgp_arm_barrier_fault)."""

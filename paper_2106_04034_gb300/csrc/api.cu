@@ -238,10 +238,26 @@ gsgp_status use_device(gsgp_ctx *c) {
 // ------------------------------------------------------------------ load --
 static gsgp_status check_shapes(gsgp_ctx *c, const float *Xtr, const float *ytr, int64_t ntr,
                                 int32_t l, const float *Xte, const float *yte, int64_t nte) {
-  if (ntr < 1) return fail(c, GSGP_E_INVALID, "n_train must be >= 1");
   if (nte < 0) return fail(c, GSGP_E_INVALID, "n_test must be >= 0");
+  if (c->sharded) {
+    // the shard's cases are the problem's cases [case0, case0 + n), training
+    // cases first: its training cases are those below n_train_all
+    const int64_t n = ntr + nte, all = c->n_train_all + c->n_test_all;
+    const int64_t want_tr = std::min(std::max(c->n_train_all - c->shard_case0, (int64_t)0), n);
+    if (n < 1 || c->shard_case0 + n > all)
+      return fail(c, GSGP_E_INVALID, "a shard holds 1 .. n_train_all + n_test_all - case0 cases");
+    if (c->shard_case0 + n < all && n % 1024 != 0)
+      return fail(c, GSGP_E_INVALID,
+                  "every shard but the last holds a multiple of 1024 cases");
+    if (ntr != want_tr)
+      return fail(c, GSGP_E_INVALID, "shard at case %lld must hold %lld training cases",
+                  (long long)c->shard_case0, (long long)want_tr);
+  } else if (ntr < 1) {
+    return fail(c, GSGP_E_INVALID, "n_train must be >= 1");
+  }
   if (l < 1 || l > 65535) return fail(c, GSGP_E_INVALID, "n_features must be in [1, 65535]");
-  if (!Xtr || !ytr) return fail(c, GSGP_E_INVALID, "training data pointers must not be NULL");
+  if ((ntr > 0 && (!Xtr || !ytr)) || (!c->sharded && (!Xtr || !ytr)))
+    return fail(c, GSGP_E_INVALID, "training data pointers must not be NULL");
   if (nte > 0 && (!Xte || !yte)) return fail(c, GSGP_E_INVALID, "test data pointers are NULL");
   if (ntr + nte > (int64_t)0x7fffff00) return fail(c, GSGP_E_INVALID, "too many fitness cases");
   return GSGP_OK;
@@ -286,8 +302,10 @@ extern "C" gsgp_status gsgp_load(gsgp_ctx *c, const float *Xtr, const float *ytr
     ~Free() { dfree(c, p); }
   } guard{c, stage};
   float *sXtr = stage, *sXte = stage + nx_tr, *sy = stage + nx_tr + nx_te;
-  CK(cudaMemcpyAsync(sXtr, Xtr, sizeof(float) * nx_tr, cudaMemcpyHostToDevice, c->stream));
-  CK(cudaMemcpyAsync(sy, ytr, sizeof(float) * (size_t)ntr, cudaMemcpyHostToDevice, c->stream));
+  if (ntr > 0) {   // a case shard may hold test cases only
+    CK(cudaMemcpyAsync(sXtr, Xtr, sizeof(float) * nx_tr, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(sy, ytr, sizeof(float) * (size_t)ntr, cudaMemcpyHostToDevice, c->stream));
+  }
   if (nte > 0) {
     CK(cudaMemcpyAsync(sXte, Xte, sizeof(float) * nx_te, cudaMemcpyHostToDevice, c->stream));
     CK(cudaMemcpyAsync(sy + ntr, yte, sizeof(float) * (size_t)nte, cudaMemcpyHostToDevice,
@@ -302,7 +320,7 @@ extern "C" gsgp_status gsgp_load(gsgp_ctx *c, const float *Xtr, const float *ytr
   CK(cudaStreamSynchronize(c->stream));
   if (bad) return fail(c, GSGP_E_INVALID, "non-finite value in the fitness cases");
   TRY(prepare_data(c, ntr, l, nte));
-  LAUNCH(1, launch_transpose(sXtr, ntr, l, c->X, c->n_pad, 0, c->stream));
+  if (ntr > 0) LAUNCH(1, launch_transpose(sXtr, ntr, l, c->X, c->n_pad, 0, c->stream));
   CK(cudaMemcpyAsync(c->t, sy, sizeof(float) * (size_t)(ntr + nte), cudaMemcpyDeviceToDevice,
                      c->stream));
   if (nte > 0) LAUNCH(1, launch_transpose(sXte, nte, l, c->X, c->n_pad, ntr, c->stream));
@@ -318,8 +336,10 @@ extern "C" gsgp_status gsgp_load_device(gsgp_ctx *c, const float *Xtr, const flo
   TRY(use_device(c));
   if (!c->d_flag) TRY(dalloc_n(c, &c->d_flag, 1));
   CK(cudaMemsetAsync(c->d_flag, 0, sizeof(unsigned), c->stream));
-  LAUNCH(1, launch_nonfinite_check(Xtr, ntr * l, c->d_flag, c->stream));
-  LAUNCH(1, launch_nonfinite_check(ytr, ntr, c->d_flag, c->stream));
+  if (ntr > 0) {
+    LAUNCH(1, launch_nonfinite_check(Xtr, ntr * l, c->d_flag, c->stream));
+    LAUNCH(1, launch_nonfinite_check(ytr, ntr, c->d_flag, c->stream));
+  }
   if (nte > 0) {
     LAUNCH(1, launch_nonfinite_check(Xte, nte * l, c->d_flag, c->stream));
     LAUNCH(1, launch_nonfinite_check(yte, nte, c->d_flag, c->stream));
@@ -329,8 +349,11 @@ extern "C" gsgp_status gsgp_load_device(gsgp_ctx *c, const float *Xtr, const flo
   CK(cudaStreamSynchronize(c->stream));
   if (bad) return fail(c, GSGP_E_INVALID, "non-finite value in the fitness cases");
   TRY(prepare_data(c, ntr, l, nte));
-  LAUNCH(1, launch_transpose(Xtr, ntr, l, c->X, c->n_pad, 0, c->stream));
-  CK(cudaMemcpyAsync(c->t, ytr, sizeof(float) * (size_t)ntr, cudaMemcpyDeviceToDevice, c->stream));
+  if (ntr > 0) {
+    LAUNCH(1, launch_transpose(Xtr, ntr, l, c->X, c->n_pad, 0, c->stream));
+    CK(cudaMemcpyAsync(c->t, ytr, sizeof(float) * (size_t)ntr, cudaMemcpyDeviceToDevice,
+                       c->stream));
+  }
   if (nte > 0) {
     LAUNCH(1, launch_transpose(Xte, nte, l, c->X, c->n_pad, ntr, c->stream));
     CK(cudaMemcpyAsync(c->t + ntr, yte, sizeof(float) * (size_t)nte, cudaMemcpyDeviceToDevice,
@@ -376,6 +399,9 @@ GenParams gen_params(gsgp_ctx *c) {
   p.n_train = (int)c->n_tr;
   p.n_cases = (int)c->N;
   p.tiles = c->tiles_interp;   // 1024-case chunks, whatever the stream shape
+  p.chunk0 = c->sharded ? (int)(c->shard_case0 / 1024) : 0;
+  p.n_train_all = c->sharded ? (int)c->n_train_all : (int)c->n_tr;
+  p.n_test_all = c->sharded ? (int)c->n_test_all : (int)(c->N - c->n_tr);
   p.ms_mode = c->cfg.ms_mode;
   p.ms = c->cfg.ms;
   p.key = make_uint2((uint32_t)(c->cfg.seed & 0xffffffffu), (uint32_t)(c->cfg.seed >> 32));
@@ -409,6 +435,8 @@ gsgp_status ensure_trace(gsgp_ctx *c, int need) {
   return GSGP_OK;
 }
 
+static gsgp_status finish_init(gsgp_ctx *c);
+
 extern "C" gsgp_status gsgp_init(gsgp_ctx *c) {
   API_GUARD(c)
   if (c->state < 1) return fail(c, GSGP_E_STATE, "gsgp_init before gsgp_load");
@@ -419,13 +447,17 @@ extern "C" gsgp_status gsgp_init(gsgp_ctx *c) {
   const bool linear = cf.init_mode == GSGP_INIT_LINEAR;
   const int Kp = linear ? cf.max_genes : (1 << (cf.pop_max_depth + 1)) - 1;
   const int Kr = linear ? cf.max_genes : (1 << (cf.rt_max_depth + 1)) - 1;
-  const int64_t key[7] = {m, r, c->n_pad, Kp, Kr, cf.sigma_dtype, cf.init_mode};
+  // chunks of the whole problem (all shards): the partial sums' row stride
+  const int64_t n_all = c->sharded ? c->n_train_all + c->n_test_all : c->N;
+  const int64_t chunks_all = (c->sharded ? n_all : c->n_pad) / 1024 +
+                             ((c->sharded ? n_all : c->n_pad) % 1024 != 0);
+  const int64_t key[8] = {m, r, c->n_pad, Kp, Kr, cf.sigma_dtype, cf.init_mode, chunks_all};
   if (memcmp(key, c->layout_key, sizeof key) != 0) {
     free_run_buffers(c);
     c->Kp = Kp;
     c->Kr = Kr;
     // partial sums per 1024-case chunk (interpreter and stream kernels)
-    c->tiles_interp = (int)((c->n_pad + 1023) / 1024);
+    c->tiles_interp = (int)chunks_all;
     const int tiles_max = c->tiles_interp;
     TRY(dalloc_n(c, &c->P_genes, (size_t)m * Kp));
     TRY(dalloc_n(c, &c->P_consts, (size_t)m * Kp));
@@ -594,6 +626,9 @@ extern "C" gsgp_status gsgp_init(gsgp_ctx *c) {
   ip.n_train = (int)c->n_tr;
   ip.n_cases = (int)c->N;
   ip.tiles = c->tiles_interp;
+  ip.chunk0 = c->sharded ? (int)(c->shard_case0 / 1024) : 0;
+  if (c->sharded)   // the other shards' chunks stay zero until the exchange
+    CK(cudaMemsetAsync(c->partial, 0, sizeof(double2) * (size_t)m * c->tiles_interp, c->stream));
   ip.protect_eps = cf.protect_eps;
   ip.n_features = c->l;
   // population semantics + squared errors (rows 0..m-1 of the pool)
@@ -632,13 +667,28 @@ extern "C" gsgp_status gsgp_init(gsgp_ctx *c) {
     CK(cudaEventRecord(c->ev_init[3], c->stream));
     c->init_timed = true;
   }
-  LAUNCH(1, launch_fitness_finalize(c->partial, c->tiles_interp, m, (int)c->n_tr, (int)c->n_te,
-                                    c->fit, c->fit_te, c->stream));
+  c->shard_pending = 0;
+  if (c->sharded) {   // the fitness waits for the other shards' chunk sums
+    c->shard_pending = 1;
+    return GSGP_OK;
+  }
+  return finish_init(c);
+  API_END(c)
+}
+
+// ComputeFitness of the initial population from the complete chunk sums,
+// and the generation-0 state.
+static gsgp_status finish_init(gsgp_ctx *c) {
+  const int m = c->cfg.pop_size;
+  const int n_tr = c->sharded ? (int)c->n_train_all : (int)c->n_tr;
+  const int n_te = c->sharded ? (int)c->n_test_all : (int)c->n_te;
+  LAUNCH(1, launch_fitness_finalize(c->partial, c->tiles_interp, m, n_tr, n_te, c->fit,
+                                    c->fit_te, c->stream));
   LAUNCH(1, launch_init_state(m, c->perm, c->fit, c->dstate, c->stream));
   if (c->gs) CK(cudaMemsetAsync(&c->gs->err, 0, sizeof(int), c->stream));
+  c->shard_pending = 0;
   c->state = 2;
   return GSGP_OK;
-  API_END(c)
 }
 
 // ---------------------------------------------------------------- evolve --
@@ -951,6 +1001,9 @@ extern "C" gsgp_status gsgp_evolve(gsgp_ctx *c, int32_t generations, double *bes
                                    double *best_test) {
   API_GUARD(c)
   if (c->state != 2) return fail(c, GSGP_E_STATE, "gsgp_evolve before gsgp_init");
+  if (c->sharded)
+    return fail(c, GSGP_E_STATE,
+                "a case shard evolves by gsgp_shard_generation and gsgp_shard_finish");
   if (generations < 0) return fail(c, GSGP_E_INVALID, "generations must be >= 0");
   if (generations == 0) return GSGP_OK;
   if ((int64_t)c->gen + generations > 0x7fffffff) return fail(c, GSGP_E_INVALID, "too many generations");
@@ -1016,6 +1069,71 @@ extern "C" gsgp_status gsgp_evolve(gsgp_ctx *c, int32_t generations, double *bes
       if (best_test) best_test[k] = h[k].y;
     }
   }
+  return GSGP_OK;
+  API_END(c)
+}
+
+// ------------------------------------------------------- case sharding --
+extern "C" gsgp_status gsgp_shard_configure(gsgp_ctx *c, int64_t case0, int64_t n_train_all,
+                                            int64_t n_test_all) {
+  API_GUARD(c)
+  if (c->state != 0) return fail(c, GSGP_E_STATE, "gsgp_shard_configure after gsgp_load");
+  if (n_train_all < 1 || n_test_all < 0 || n_train_all + n_test_all > (int64_t)0x7fffff00)
+    return fail(c, GSGP_E_INVALID, "need n_train_all >= 1, n_test_all >= 0");
+  if (case0 < 0 || case0 % 1024 != 0 || case0 >= n_train_all + n_test_all)
+    return fail(c, GSGP_E_INVALID, "case0 must be a multiple of 1024 below the case count");
+  c->sharded = true;
+  c->shard_case0 = case0;
+  c->n_train_all = n_train_all;
+  c->n_test_all = n_test_all;
+  return GSGP_OK;
+  API_END(c)
+}
+
+extern "C" gsgp_status gsgp_shard_partials(gsgp_ctx *c, double **partials, int64_t *rows,
+                                           int64_t *chunks) {
+  API_GUARD(c)
+  if (!c->sharded) return fail(c, GSGP_E_STATE, "not a case shard");
+  if (!c->shard_pending)
+    return fail(c, GSGP_E_STATE, "no exchange is pending (after gsgp_init or a generation)");
+  if (partials) *partials = reinterpret_cast<double *>(c->partial);
+  if (rows) *rows = c->cfg.pop_size;
+  if (chunks) *chunks = c->tiles_interp;
+  return GSGP_OK;
+  API_END(c)
+}
+
+extern "C" gsgp_status gsgp_shard_generation(gsgp_ctx *c) {
+  API_GUARD(c)
+  if (!c->sharded) return fail(c, GSGP_E_STATE, "not a case shard");
+  if (c->state != 2 || c->shard_pending)
+    return fail(c, GSGP_E_STATE, "gsgp_shard_generation needs a finished init or generation");
+  if (c->gen == 0x7fffffff) return fail(c, GSGP_E_INVALID, "too many generations");
+  TRY(use_device(c));
+  TRY(ensure_trace(c, c->gen + 1));
+  const GenParams p = gen_params(c);
+  // this shard's chunk columns are rewritten by the stream; the others must
+  // be zero, so that summing the shards' arrays assembles the whole
+  CK(cudaMemsetAsync(c->partial, 0, sizeof(double2) * (size_t)p.m * c->tiles_interp, c->stream));
+  LAUNCH(1, launch_select(p, c->stream, false));
+  LAUNCH(1, launch_stream(p, c->cfg.sigma_dtype == GSGP_SIGMA_BF16, GenShape{1, 8}, c->stream,
+                          false));
+  c->shard_pending = 2;
+  return GSGP_OK;
+  API_END(c)
+}
+
+extern "C" gsgp_status gsgp_shard_finish(gsgp_ctx *c) {
+  API_GUARD(c)
+  if (!c->sharded) return fail(c, GSGP_E_STATE, "not a case shard");
+  if (!c->shard_pending) return fail(c, GSGP_E_STATE, "no exchange is pending");
+  TRY(use_device(c));
+  if (c->shard_pending == 1) return finish_init(c);
+  const GenParams p = gen_params(c);
+  LAUNCH(1, launch_final(p, c->stream, false));
+  c->gen += 1;
+  c->model_gen = -1;
+  c->shard_pending = 0;
   return GSGP_OK;
   API_END(c)
 }

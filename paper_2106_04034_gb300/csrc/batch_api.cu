@@ -98,7 +98,7 @@ void free_graph(gsgp_batch *b) {
 
 // GenParams has no padding, so launch arguments built from zeroed storage
 // compare equal byte for byte exactly when their values are equal.
-static_assert(sizeof(GenParams) == 12 * sizeof(void *) + 8 + 8 * 4 + 8 + 8 + 8,
+static_assert(sizeof(GenParams) == 12 * sizeof(void *) + 8 + 8 * 4 + 8 + 8 + 8 + 8,
               "GenParams padding");
 
 int64_t run_items(const gsgp_ctx *c, const GenShape &sh) {
@@ -349,7 +349,7 @@ extern "C" gsgp_status gsgp_batch_create(gsgp_ctx *const *runs, int32_t count, g
       if (runs[q] == runs[k]) return GSGP_E_INVALID;   // a run appears once
   }
   for (int32_t k = 0; k < count; ++k)
-    if (runs[k]->state != 2) return GSGP_E_STATE;
+    if (runs[k]->state != 2 || runs[k]->sharded) return GSGP_E_STATE;
   const int dev = runs[0]->device;
   const int32_t dtype = runs[0]->cfg.sigma_dtype;
   for (int32_t k = 1; k < count; ++k)

@@ -106,6 +106,7 @@ gsgp_status target_hash(gsgp_ctx *c, uint64_t *out) {
 extern "C" gsgp_status gsgp_checkpoint(gsgp_ctx *c, void *buf, size_t cap, size_t *size_out) {
   API_GUARD(c)
   if (c->state != 2) return fail(c, GSGP_E_STATE, "gsgp_checkpoint before gsgp_init");
+  if (c->sharded) return fail(c, GSGP_E_STATE, "checkpoints of case shards are not supported");
   const int gen = c->gen;
   const size_t total = sizeof(Header) + payload_bytes(c, gen);
   if (size_out) *size_out = total;
@@ -157,6 +158,7 @@ extern "C" gsgp_status gsgp_checkpoint(gsgp_ctx *c, void *buf, size_t cap, size_
 extern "C" gsgp_status gsgp_restore(gsgp_ctx *c, const void *buf, size_t size) {
   API_GUARD(c)
   if (c->state < 1) return fail(c, GSGP_E_STATE, "gsgp_restore before gsgp_load");
+  if (c->sharded) return fail(c, GSGP_E_STATE, "checkpoints of case shards are not supported");
   if (!buf || size < sizeof(Header)) return fail(c, GSGP_E_INVALID, "checkpoint too short");
   Header h;
   memcpy(&h, buf, sizeof h);

@@ -98,7 +98,7 @@ struct GenParams {
   int *perm;                 // [2][2m]: rows of population slots, then free rows
   double *fit;               // [2][m] training RMSE
   double *fit_te;            // [2][m] test RMSE
-  double2 *partial;          // [m][tiles] per-tile (train, test) squared errors
+  double2 *partial;          // [m][tiles] per-chunk (train, test) squared errors
   int4 *sel;                 // [m] (parent row, offspring row, rt1, rt2) of this generation
   float *sel_ms;             // [m] mutation step of this generation
   int4 *trace;               // [gcap][m] (parent slot, rt1, rt2, ms bits)
@@ -106,15 +106,20 @@ struct GenParams {
   DevState *state;
   int64_t n_pad;
   int m, r, tsize;
-  int n_train, n_cases;
-  int tiles;
+  int n_train, n_cases;      // cases held by this context (train first)
+  int tiles;                 // 1024-case chunks of the whole problem: row stride of partial
   int ms_mode;
   float ms;
   uint2 key;
   uint32_t run;
   int elitism;
   float p_crossover;         // probability of geometric semantic crossover (0: mutation only)
-  int reserved;
+  // Case sharding: this context's cases are the problem's cases from chunk
+  // chunk0 on (its chunk c is column chunk0 + c of partial); the RMSE
+  // divides by the whole problem's training / test case counts.  Unsharded:
+  // chunk0 = 0, n_train_all = n_train, n_test_all = n_cases - n_train.
+  int chunk0;
+  int n_train_all, n_test_all;
 };
 
 // Parameters of the interpreter (ComputeSemantics) kernel.
@@ -127,7 +132,7 @@ struct InterpParams {
   int K;                     // row stride of genes / consts
   int max_len;               // longest program of the pool (sizes shared memory)
   void *out;                 // [count][n_pad] float (population) or sigma (random)
-  double2 *partial;          // [count][tiles] (population only)
+  double2 *partial;          // [count][tiles] (population only); chunk c at column chunk0 + c
   int64_t n_pad;
   int n_train, n_cases;
   int tiles;
@@ -135,6 +140,7 @@ struct InterpParams {
   float protect_eps;
   const int *order;          // programs of this launch (CTA column x runs order[x]), or null
   int n_features;            // rows of X
+  int chunk0;                // first chunk of partial this context writes (case sharding)
 };
 
 }  // namespace gsgp

@@ -26,9 +26,15 @@ struct gsgp_ctx {
   float *X = nullptr;   // [l][n_pad]
   float *t = nullptr;   // [n_pad]
 
+  // case sharding (gsgp_shard_configure): this context holds the problem's
+  // cases [shard_case0, shard_case0 + N) of n_train_all + n_test_all
+  bool sharded = false;
+  int64_t shard_case0 = 0, n_train_all = 0, n_test_all = 0;
+  int shard_pending = 0;   // 1: initial fitness, 2: a generation's survival awaits the exchange
+
   // run state
   int Kp = 0, Kr = 0;
-  int tiles_interp = 0;   // 1024-case chunks of a semantic row
+  int tiles_interp = 0;   // 1024-case chunks of the whole problem: row stride of partial
   // generation loop: path 1 = persistent cooperative kernel, 2 = chained
   // select/stream/final launches; shape = (float4 chunks per thread,
   // offspring per CTA); grid = CTAs of the persistent kernel
@@ -46,7 +52,7 @@ struct gsgp_ctx {
   int *bk_perm = nullptr;    // state snapshot used while autotuning
   double *bk_fit = nullptr, *bk_fit_te = nullptr;
   DevState *bk_state = nullptr;
-  int64_t layout_key[7] = {0, 0, 0, 0, 0, 0, 0};
+  int64_t layout_key[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   int *P_genes = nullptr, *P_len = nullptr, *R_genes = nullptr, *R_len = nullptr;
   float *P_consts = nullptr, *R_consts = nullptr;
   // the programs the interpreter and the model evaluate: the live code of

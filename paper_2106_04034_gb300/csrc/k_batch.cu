@@ -137,8 +137,8 @@ __global__ void __launch_bounds__(kGenThreads, 4) batch_kernel(const __grid_cons
         const double2 sse = warp_sum_partials(p.partial + (size_t)i * p.tiles, p.tiles, lane);
         if (lane == 0) {
           const int par = __ldcg(&p.state->parity);
-          p.fit[(size_t)(par ^ 1) * p.m + i] = rmse_from_sse(sse.x, p.n_train);
-          p.fit_te[(size_t)(par ^ 1) * p.m + i] = rmse_from_sse(sse.y, p.n_cases - p.n_train);
+          p.fit[(size_t)(par ^ 1) * p.m + i] = rmse_from_sse(sse.x, p.n_train_all);
+          p.fit_te[(size_t)(par ^ 1) * p.m + i] = rmse_from_sse(sse.y, p.n_test_all);
         }
       }
     }

@@ -85,8 +85,8 @@ __global__ void __launch_bounds__(kFinalThreads) final_kernel(const GenParams p)
   if (i < m) {
     const double2 sse = warp_sum_partials(p.partial + (size_t)i * p.tiles, p.tiles, lane);
     if (lane == 0) {
-      p.fit[(size_t)(par ^ 1) * m + i] = rmse_from_sse(sse.x, p.n_train);
-      p.fit_te[(size_t)(par ^ 1) * m + i] = rmse_from_sse(sse.y, p.n_cases - p.n_train);
+      p.fit[(size_t)(par ^ 1) * m + i] = rmse_from_sse(sse.x, p.n_train_all);
+      p.fit_te[(size_t)(par ^ 1) * m + i] = rmse_from_sse(sse.y, p.n_test_all);
       __threadfence();
     }
   }
@@ -152,7 +152,8 @@ cudaError_t launch_stream(const GenParams &p, int sigma_bf16, const GenShape &sh
                           bool pdl) {
   if (!gen_shape_supported(sh)) return cudaErrorInvalidValue;
   const int groups = (p.m + sh.opb - 1) / sh.opb;
-  const unsigned grid = (unsigned)((int64_t)p.tiles * groups);
+  const int64_t chunks = (p.n_pad + 1023) / 1024;   // this context's 1024-case chunks
+  const unsigned grid = (unsigned)(chunks * groups);
   return sigma_bf16 ? stream_vec<__nv_bfloat16>(p, sh, grid, s, pdl)
                     : stream_vec<float>(p, sh, grid, s, pdl);
 }

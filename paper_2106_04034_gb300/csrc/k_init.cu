@@ -608,8 +608,8 @@ __global__ void __launch_bounds__(kInterpThreads) interpret_kernel(InterpParams 
       if (lane == 0) s_sub[q][warp] = sub;
     }
     __syncthreads();
-    if (tid < VEC && tile * VEC + tid < p.tiles)
-      p.partial[(size_t)prog * p.tiles + tile * VEC + tid] = chunk_total(s_sub[tid]);
+    if (tid < VEC && tile * VEC + tid < (int)((p.n_pad + 1023) >> 10))
+      p.partial[(size_t)prog * p.tiles + p.chunk0 + tile * VEC + tid] = chunk_total(s_sub[tid]);
   } else {
 #pragma unroll
     for (int q = 0; q < VEC; ++q) {

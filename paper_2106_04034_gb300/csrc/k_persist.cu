@@ -161,9 +161,9 @@ __device__ __forceinline__ void fitness_phase(const GenParams &p, const PersistA
       const int ii = r0 + tid * nb + b;
       if (ii < m) {
         const double2 sse = s_sse[tid];
-        const double f = rmse_from_sse(sse.x, p.n_train);
+        const double f = rmse_from_sse(sse.x, p.n_train_all);
         fo[ii] = f;
-        fo_te[ii] = rmse_from_sse(sse.y, p.n_cases - p.n_train);
+        fo_te[ii] = rmse_from_sse(sse.y, p.n_test_all);
         const unsigned long long k = fit_key(f);
         if (arg_better<false>(k, ii, mn, imn)) {
           mn = k;
@@ -542,8 +542,9 @@ __global__ void __launch_bounds__(kTmaThreads, 1) persist_tma_kernel(const GenPa
           if (lane < VEC) {   // lane v finishes chunk v
             const UnitMeta mt = meta[slot];
             const int chunk = mt.tile * VEC + lane;
-            if (chunk < p.tiles)
-              p.partial[(size_t)mt.i * p.tiles + chunk] = chunk_total(s_sub[slot][lane]);
+            if (chunk < (int)((p.n_pad + 1023) >> 10))
+              p.partial[(size_t)mt.i * p.tiles + p.chunk0 + chunk] =
+                  chunk_total(s_sub[slot][lane]);
           }
           __syncwarp();
         }

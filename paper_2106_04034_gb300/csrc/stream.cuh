@@ -433,11 +433,12 @@ __device__ __forceinline__ void stream_item_pipe_bf16x2(const GenParams &p, int 
 template <int VEC, int OPB>
 __device__ __forceinline__ void item_partials(const GenParams &p, int tile, int i0, int cnt,
                                               const ItemSums<VEC, OPB> &sum) {
+  const int chunks = (int)((p.n_pad + 1023) >> 10);   // this context's chunks
   for (int e = threadIdx.x; e < cnt * VEC; e += kGenThreads) {
     const int k = e / VEC, v = e - k * VEC;
     const int chunk = tile * VEC + v;
-    if (chunk < p.tiles)
-      p.partial[(size_t)(i0 + k) * p.tiles + chunk] = chunk_total(sum[k][v]);
+    if (chunk < chunks)
+      p.partial[(size_t)(i0 + k) * p.tiles + p.chunk0 + chunk] = chunk_total(sum[k][v]);
   }
 }
 
