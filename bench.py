@@ -495,14 +495,16 @@ def run_batched(args, rank, world, local_rank):
         batch.evolve(G, log=False)
         return [r.predict(d[2]) for r, d in zip(runs, hdatas)]
 
-    step_host()
-    barrier()
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
+    e2e_s = float("nan")
+    if not getattr(args, "skip_e2e", False):
         step_host()
-    barrier()
-    e2e_s = (time.perf_counter() - t0) / args.steps
-    e2e_s = max_over_ranks(e2e_s, world)
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            step_host()
+        barrier()
+        e2e_s = (time.perf_counter() - t0) / args.steps
+        e2e_s = max_over_ranks(e2e_s, world)
     h2d = sum(sum(a.nbytes for a in d) + d[2].nbytes for d in datas)
     d2h = sum(w.n_test * 8 for w in ws)
     batch.close()
@@ -723,6 +725,88 @@ def run_reference(args, rank):
     }
 
 
+def time_run(w: W.Workload, data, steps: int = 1, warmup_gens: int = 64):
+    """One workload on this GPU through the same step as the headline
+    (load_device + init + evolve(G) + best_trace + predict(test)): the
+    autotuner's choice is made on an untimed warm-up of warmup_gens
+    generations; then `steps` timed steps.  Returns updates/s, ms per step,
+    the stream kernel's fraction of the measured HBM peak and its shape."""
+    import torch
+
+    import paper_2106_04034_gb300 as pkg
+    dev = [torch.from_numpy(a).cuda() for a in data]
+    stream = torch.cuda.current_stream()
+    run = pkg.Run(make_config(pkg, w, stream))
+    y = torch.zeros(max(w.n_test, 1), dtype=torch.float64, device="cuda")
+    run.load_device(*dev)
+    run.init()
+    run.evolve(min(warmup_gens, w.generations), log=False)
+
+    def step():
+        run.load_device(*dev)
+        run.init()
+        run.evolve(w.generations, log=False)
+        run.best_trace()
+        run.predict_device(dev[2], y)
+
+    torch.cuda.synchronize()
+    run.set_kernel_timing(True)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    kms = run.kernel_times(1 << 22)
+    run.set_kernel_timing(False)
+    ms = e0.elapsed_time(e1) / steps
+    info = run.info()
+    ub = unique_bytes_per_generation(run, w, 2 if w.sigma_bf16 else 4)
+    per = info.evolve_generations_per_launch
+    bounds = list(range(0, w.generations, per)) + [w.generations]
+    per_launch = np.array([ub[a:b].sum() for a, b in zip(bounds[:-1], bounds[1:])])
+    achieved = float(per_launch.sum()) * steps / (float(kms.sum()) / 1e3) / 1e9
+    peak, _ = measured_peak_gbs()
+    run.close()
+    return {"value": float(w.pop_size) * w.n_cases * w.generations / (ms / 1e3), "unit": UNIT,
+            "ms_per_step": ms, "steps": steps, "generations": w.generations,
+            "stream_frac_of_measured_hbm": achieved / peak,
+            "shape": [info.evolve_tile_cases // 1024, info.evolve_offspring_per_cta]}
+
+
+def measure_variants(args):
+    """The other workloads of the benchmark on the same GPU as the headline
+    (one timed step each after an untimed autotuning warm-up), so that their
+    comparisons are made on one machine: the mid workload (C2); the
+    precision variant (large workload, G = 2000, sigma(R) stored bf16)
+    against the same run with float32 sigma on the same data (C4); 48
+    batched runs against the same runs evolved one after another (C5)."""
+    out = {}
+    mid = W.MID
+    out["mid"] = time_run(mid, W.make_data(mid), steps=3)
+    out["mid"]["workload"] = mid.name
+    big = W.LARGE.replace(generations=2000)
+    data = W.make_data(big)
+    f32 = time_run(big, data)
+    bf16 = time_run(W.LARGE_BF16, data)
+    out["large_bf16"] = {"workload": W.LARGE_BF16.name, "bf16_sigma": bf16, "f32_sigma": f32,
+                         "speedup_bf16_over_f32": bf16["value"] / f32["value"]}
+    del data
+    bargs = argparse.Namespace(**vars(args))
+    bargs.steps, bargs.warmup, bargs.shape, bargs.generations = 1, 1, "", 0
+    bargs.skip_e2e = True
+    line, _ = run_batched(bargs, 0, 1, 0)
+    out["batched"] = {"workload": line["config"]["workload"], "value": line["value"],
+                      "unit": UNIT, "ms_per_step": line["ms_per_step"],
+                      "sequential": line["sequential"],
+                      "speedup_batched_over_sequential":
+                          line["value"] / line["sequential"]["value"],
+                      "stream_frac_of_measured_hbm": line["roofline"]["frac"],
+                      "shape": line["roofline"]["shape"]}
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -743,6 +827,8 @@ def main():
                     help="runs of the batched workload")
     ap.add_argument("--max-train", type=int, default=0,
                     help="cap on n_train of the batched workload's runs (0: none)")
+    ap.add_argument("--no-variants", action="store_true",
+                    help="skip the mid / bf16 / batched comparison runs of the default workload")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -771,6 +857,10 @@ def main():
         w = min(ws, key=lambda x: x.pop_size * x.n_cases).replace(run=0)
     else:
         line, w = run_ours(args, rank, world, local_rank)
+        if (world == 1 and args.workload == "large" and not args.no_variants
+                and not args.generations and not args.pop_size and not args.shape
+                and not args.p_crossover):
+            line["variants"] = measure_variants(args)
     if rank == 0:
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(w.replace(run=0))

@@ -79,3 +79,38 @@ def _features_file(tmp_path, X):
     f = tmp_path / "features.txt"
     np.savetxt(f, X, fmt="%.9g")
     return f
+
+
+def test_cli_fitness_files_against_the_oracle(tmp_path):
+    """The tool's per-generation best training and test RMSE (the paper's
+    two output series, Sec. 3.3) against the float64 oracle run from the
+    same seed on the same case files, independently (programs, semantics,
+    selection and survival all its own): the oracle's best-of-generation
+    series must agree within the RMSE tolerance."""
+    from oracle import gsgp as og
+    from gpu_util import RMSE_RTOL, oracle_params
+    build_library()
+    w = W.TINY.replace(pop_size=64, n_random_trees=50)
+    Xtr, ytr, Xte, yte = W.make_data(w)
+    write_cases(tmp_path / "train.txt", Xtr, ytr)
+    write_cases(tmp_path / "test.txt", Xte, yte)
+    tr_rows = np.loadtxt(tmp_path / "train.txt", dtype=np.float64).astype(np.float32)
+    te_rows = np.loadtxt(tmp_path / "test.txt", dtype=np.float64).astype(np.float32)
+    (tmp_path / "config.ini").write_text(
+        "[run]\n"
+        f"pop_size = {w.pop_size}\nn_random_trees = {w.n_random_trees}\n"
+        f"pop_max_depth = {w.pop_max_depth}\nrt_max_depth = {w.rt_max_depth}\n"
+        f"generations = {G}\nruns = 2\n")
+    r = subprocess.run([CLI, "-train_file", str(tmp_path / "train.txt"), "-test_file",
+                        str(tmp_path / "test.txt"), "-config", str(tmp_path / "config.ini"),
+                        "-output_dir", str(tmp_path)], capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr
+    ftr = np.loadtxt(tmp_path / "fitness_train.txt", ndmin=2)
+    fte = np.loadtxt(tmp_path / "fitness_test.txt", ndmin=2)
+    for k in range(2):
+        ref = og.GSGP(oracle_params(w.replace(run=k)), tr_rows[:, :-1], tr_rows[:, -1],
+                      te_rows[:, :-1], te_rows[:, -1])
+        ref.init()
+        ref.evolve(G)
+        assert np.allclose(ftr[:, k], ref.best_train, rtol=RMSE_RTOL, atol=0)
+        assert np.allclose(fte[:, k], ref.best_test, rtol=RMSE_RTOL, atol=0)
