@@ -38,7 +38,8 @@ METRIC = "semantic updates/s (pop·n·gens/s) and % of HBM peak, vs plain FP32 a
 UNIT = "semantic updates/s"
 PROFILE_DIR = os.path.join(ROOT, "profiles")
 GEN_KERNEL_SRC = [os.path.join(ROOT, "paper_2106_04034_gb300", "csrc", f)
-                  for f in ("k_persist.cu", "k_generation.cu", "stream.cuh", "common.cuh")]
+                  for f in ("k_persist.cu", "k_generation.cu", "stream.cuh", "common.cuh",
+                            "reduce.cuh", "gridsync.cuh", "kernels.cuh")]
 
 
 def measured_peak_gbs():
@@ -90,11 +91,14 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(workload_name: str):
-    """DRAM bytes per generation of the generation kernel from the committed
-    ncu summary of this workload (profiles/persist_kernel_<workload>.txt), if
-    it was taken with the current kernel sources (else None).  Summaries of a
-    smaller capture state the traffic scaled to the workload's full size."""
+def profiled_traffic(workload_name: str, shape):
+    """DRAM traffic of the generation kernel from the committed ncu summary
+    of this workload (profiles/persist_kernel_<workload>.txt), if it was
+    taken with the current kernel sources and holds the stream shape in use
+    (else None): the measured ratio of DRAM bytes to the algorithmic bytes of the
+    captured launch.  The caller multiplies it by its own launches'
+    algorithmic bytes (a generation's traffic changes over a run as the
+    population's distinct parents do, the ratio does not)."""
     try:
         src = kernel_source_hash()
         short = workload_name.split(":")[0].strip().replace("-", "_")
@@ -105,7 +109,7 @@ def profiled_traffic(workload_name: str):
                 kv[k.strip()] = v.strip()
         if kv.get("kernel_source_sha256_16") != src or kv.get("workload") != workload_name:
             return None
-        return float(kv["traffic_bytes_per_generation"])
+        return float(kv[f"traffic_to_algorithmic[{shape[0]},{shape[1]}]"])
     except Exception:
         return None
 
@@ -276,8 +280,9 @@ def run_ours(args, rank, world, local_rank):
     avg_ms = float(kms.mean())
     achieved = total_bytes / (float(kms.sum()) / 1e3) / 1e9
     peak, peak_kind = measured_peak_gbs()
-    per_gen_traffic = profiled_traffic(w.name)
-    traffic = None if per_gen_traffic is None else per_gen_traffic * G / per_launch.size
+    ratio = profiled_traffic(w.name, (info.evolve_tile_cases // 1024,
+                                      info.evolve_offspring_per_cta))
+    traffic = None if ratio is None else ratio * avg_bytes
     stream_roofline = {
         "kernel": kname, "bound": "hbm", "achieved": achieved, "peak": peak,
         "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,

@@ -134,7 +134,9 @@ __global__ void __launch_bounds__(kGenThreads, 4) batch_kernel(const __grid_cons
         r = advance_run(a.m_off, r, gw);
         const GenParams &p = a.runs[r];
         const int i = gw - a.m_off[r];
-        const double2 sse = warp_sum_partials(p.partial + (size_t)i * p.tiles, p.tiles, lane);
+        const double2 *row = p.partial + (size_t)i * p.tiles;
+        const double2 sse = VEC == 2 && p.tiles > 128 ? warp_sum_partials_long(row, p.tiles, lane)
+                                                      : warp_sum_partials(row, p.tiles, lane);
         if (lane == 0) {
           const int par = __ldcg(&p.state->parity);
           p.fit[(size_t)(par ^ 1) * p.m + i] = rmse_from_sse(sse.x, p.n_train_all);

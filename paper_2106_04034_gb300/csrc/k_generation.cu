@@ -83,7 +83,9 @@ __global__ void __launch_bounds__(kFinalThreads) final_kernel(const GenParams p)
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int i = blockIdx.x * kFinalWarps + warp;
   if (i < m) {
-    const double2 sse = warp_sum_partials(p.partial + (size_t)i * p.tiles, p.tiles, lane);
+    const double2 *row = p.partial + (size_t)i * p.tiles;
+    const double2 sse = p.tiles > 128 ? warp_sum_partials_long(row, p.tiles, lane)
+                                      : warp_sum_partials(row, p.tiles, lane);
     if (lane == 0) {
       p.fit[(size_t)(par ^ 1) * m + i] = rmse_from_sse(sse.x, p.n_train_all);
       p.fit_te[(size_t)(par ^ 1) * m + i] = rmse_from_sse(sse.y, p.n_test_all);

@@ -671,7 +671,9 @@ __global__ void __launch_bounds__(256)
   const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (i >= count) return;
-  const double2 sse = warp_sum_partials(partial + (size_t)i * tiles, tiles, lane);
+  const double2 *row = partial + (size_t)i * tiles;
+  const double2 sse = tiles > 128 ? warp_sum_partials_long(row, tiles, lane)
+                                  : warp_sum_partials(row, tiles, lane);
   if (lane == 0) {
     fit[i] = rmse_from_sse(sse.x, n_train);
     fit_te[i] = rmse_from_sse(sse.y, n_test);

@@ -141,6 +141,10 @@ __device__ __forceinline__ void select_phase(const GenParams &p, const GenState 
 // fixed lane-strided order and one thread per offspring then takes the RMSE
 // (the phase's only float64 division and square root).  Each CTA publishes
 // the arg-min and arg-max (fitness key, first index) of its offspring.
+// kLongRows: rows of more than 128 chunks are summed by the unrolled,
+// not-inlined warp_sum_partials_long (same order, same result); only the
+// kernels whose streaming code keeps its registers with that call use it.
+template <bool kLongRows>
 __device__ __forceinline__ void fitness_phase(const GenParams &p, const PersistArgs &x, int par, int b,
                                            int nb, double2 *s_sse) {
   constexpr int NW = kGenThreads / 32;
@@ -153,7 +157,9 @@ __device__ __forceinline__ void fitness_phase(const GenParams &p, const PersistA
   for (int r0 = 0; r0 < m; r0 += nb * NW) {
     const int i = r0 + warp * nb + b;
     if (warp < NW && i < m) {
-      const double2 sse = warp_sum_partials(p.partial + (size_t)i * p.tiles, p.tiles, lane);
+      const double2 *row = p.partial + (size_t)i * p.tiles;
+      const double2 sse = kLongRows && p.tiles > 128 ? warp_sum_partials_long(row, p.tiles, lane)
+                                                     : warp_sum_partials(row, p.tiles, lane);
       if (lane == 0) s_sse[warp] = sse;
     }
     __syncthreads();
@@ -366,7 +372,7 @@ __global__ void __launch_bounds__(kGenThreads, 4) persist_kernel(const GenParams
     if (!barrier()) return;
 
     // ---------------- F1: offspring RMSE ----------------------------------
-    fitness_phase(p, x, st.par, b, nb, s_sse);
+    fitness_phase<VEC == 2>(p, x, st.par, b, nb, s_sse);
     if (!barrier()) return;
 
     // ---------------- F2: survival with elitism ---------------------------
@@ -672,7 +678,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1) persist_tma_kernel(const GenPa
     u0 += (unsigned)nunits;
     if (!barrier()) return;
 
-    fitness_phase(p, x, st.par, b, nb, s_sse);
+    fitness_phase<false>(p, x, st.par, b, nb, s_sse);
     if (!barrier()) return;
 
     survive_phase(p, x, st, b, nb, it + 1 == x.G, s_min, s_max);
