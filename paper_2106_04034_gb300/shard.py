@@ -50,15 +50,31 @@ def slice_cases(data: Sequence[np.ndarray], case0: int, n_tr: int, n_te: int):
             X_te[a_te:a_te + n_te], y_te[a_te:a_te + n_te])
 
 
+def _foreign_streams(runs) -> bool:
+    """True when a run's work is not queued on torch's current stream (the
+    exchange, a torch operation, then needs a device synchronisation on each
+    side)."""
+    import torch
+    cur = torch.cuda.current_stream().cuda_stream
+    return any((r.cfg.stream or 0) != cur for r in runs)
+
+
 def local_sum(runs) -> None:
-    """Exchange for shards that share one process and one stream: every
-    shard's array becomes the element-wise sum of all of them."""
+    """Exchange for shards that share one process: every shard's array
+    becomes the element-wise sum of all of them (on torch's current stream;
+    runs on other streams are synchronised around it)."""
+    import torch
+    sync = _foreign_streams(runs)
+    if sync:
+        torch.cuda.synchronize()
     arrays = [r.shard_partials() for r in runs]
     total = arrays[0].clone()
     for a in arrays[1:]:
         total += a
     for a in arrays:
         a.copy_(total)
+    if sync:
+        torch.cuda.synchronize()
 
 
 def init(runs, exchange: Callable[[list], None] = local_sum) -> None:
@@ -82,11 +98,17 @@ def evolve(runs, generations: int, exchange: Callable[[list], None] = local_sum)
 
 def allreduce_exchange(group=None) -> Callable[[list], None]:
     """Exchange for one shard per rank: an all-reduce (sum) of the shard's
-    array over the process group (torch.distributed, queued on the current
-    stream, which must be the shard's stream)."""
+    array over the process group (torch.distributed, ordered with torch's
+    current stream; a shard on another stream is synchronised around it)."""
+    import torch
     import torch.distributed as dist
 
     def ex(runs):
+        sync = _foreign_streams(runs)
+        if sync:
+            torch.cuda.synchronize()
         for r in runs:
             dist.all_reduce(r.shard_partials(), op=dist.ReduceOp.SUM, group=group)
+        if sync:
+            torch.cuda.synchronize()
     return ex
