@@ -6,7 +6,8 @@ one unsharded run over all the cases, and the same model.  The shards run on
 one GPU here, driven from one process; the exchange is the element-wise sum
 of their arrays (on several GPUs it is an all-reduce).  Cases: two and three
 shards, a train/test boundary inside a shard and inside a chunk, a shard
-with test cases only, a ragged last chunk, bf16 sigma and crossover."""
+with test cases only, a ragged last chunk, bf16 sigma, crossover and the
+paper's linear genomes."""
 import numpy as np
 import pytest
 
@@ -33,6 +34,7 @@ CASES = {
     "test-only shard": (MID_S.replace(n_train=2000, n_test=3000), 3, {}),
     "bf16 sigma": (MID_S.replace(sigma_bf16=True), 2, {}),
     "crossover": (MID_S, 3, {"p_crossover": 0.5}),
+    "linear genomes": (MID_S.replace(init_mode=1, max_genes=127), 2, {}),
 }
 
 
@@ -57,7 +59,7 @@ def _config_run(w, over):
         const_hi=p.const_hi, protect_eps=p.protect_eps, ms=p.ms,
         tournament_size=p.tournament_size,
         sigma_dtype=pkg.SIGMA_BF16 if p.sigma_bf16 else pkg.SIGMA_F32,
-        p_crossover=p.p_crossover)
+        init_mode=p.init_mode, max_genes=p.max_genes, p_crossover=p.p_crossover)
     cfg.stream = torch.cuda.current_stream().cuda_stream
     return pkg.Run(cfg)
 
