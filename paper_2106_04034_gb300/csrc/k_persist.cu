@@ -381,21 +381,25 @@ __global__ void __launch_bounds__(kGenThreads, 4) persist_kernel(const GenParams
 }
 
 // ---------------------------------------------------------------------------
-// TMA-staged variant of the mutation stream.  A producer warp (warp 8) keeps
+// TMA-staged variant of the mutation stream.  A producer warp (warp 16) keeps
 // up to S units in flight: for each unit (one offspring x one tile of
-// W = 1024 * VEC cases) its lane 0 issues four bulk asynchronous copies
+// W = 1024 * VEC cases) its lane 0 issues three bulk asynchronous copies
 // (cp.async.bulk, global -> shared, completion counted in bytes on the
-// unit's "full" mbarrier): the parent row segment, the targets of the tile
-// and the two sigma(R) row segments.  The 8 consumer warps take every unit
-// in order: wait on "full", compute the offspring from shared memory with the
-// thread-to-case map of the other kernels, store it, leave their sub-block
-// totals in shared memory and arrive on the unit's "empty" mbarrier.  The
-// producer warp then finishes the unit's chunk sums (canonical order) and
-// reuses the slot, so the memory system always has up to S units requested.
+// unit's "full" mbarrier): the parent row segment and the two sigma(R) row
+// segments, 4 KB * VEC each.  The 16 consumer warps take every unit in
+// order: wait on "full", compute the offspring from shared memory (warp w
+// takes sub-block w % 8 of chunks w / 8, w / 8 + 2, ..., 4 cases per lane,
+// the targets read through L2 before the wait), store it, leave their
+// sub-block totals in shared memory and arrive on the unit's "empty"
+// mbarrier.  The producer warp then finishes the unit's chunk sums
+// (canonical order) and reuses the slot.  A bulk copy streams HBM at the
+// copy rate only when it is large (measured on this GPU: 1.7 TB/s with
+// 4 KB copies from one producer lane per SM, 6.8 TB/s with 16 KB copies),
+// so the useful shapes are VEC = 4 (16 KB copies) and VEC = 2.
 // ---------------------------------------------------------------------------
-constexpr int kTmaConsumerWarps = kGenThreads / 32;            // 8
-constexpr int kTmaThreads = kGenThreads + 32;                  // + producer warp
-constexpr int kTmaSmemBudget = 176 * 1024;   // stage buffers; the rest is static smem
+constexpr int kTmaConsumerWarps = 16;
+constexpr int kTmaThreads = kTmaConsumerWarps * 32 + 32;      // + producer warp
+constexpr int kTmaSmemBudget = 200 * 1024;   // stage buffers; the rest is static smem
 
 __device__ __forceinline__ uint32_t smem_u32(const void *ptr) {
   return (uint32_t)__cvta_generic_to_shared(ptr);
@@ -454,8 +458,8 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity, GridSy
 template <typename SigT, int VEC>
 struct TmaCfg {
   static constexpr int W = 1024 * VEC;
-  // parent row segment, target segment (float), two sigma(R) row segments
-  static constexpr int kStageBytes = W * (int)(2 * sizeof(float) + 2 * sizeof(SigT));
+  // parent row segment (float), two sigma(R) row segments
+  static constexpr int kStageBytes = W * (int)(sizeof(float) + 2 * sizeof(SigT));
   static constexpr int S0 = kTmaSmemBudget / kStageBytes;
   static constexpr int S = S0 > 16 ? 16 : S0;   // stages
   static constexpr int kSmem = S * kStageBytes;
@@ -476,9 +480,9 @@ __global__ void __launch_bounds__(kTmaThreads, 1) persist_tma_kernel(const GenPa
   extern __shared__ __align__(128) unsigned char stage_mem[];
   __shared__ __align__(8) uint64_t full_bar[S], empty_bar[S];
   __shared__ UnitMeta meta[S];
-  __shared__ float2 s_sub[S][VEC][NW];   // per unit and chunk: sub-block totals
+  __shared__ float2 s_sub[S][VEC][8];    // per unit and chunk: sub-block totals
   __shared__ ulonglong2 s_min[32], s_max[32];
-  __shared__ double2 s_sse[NW];
+  __shared__ double2 s_sse[kGenThreads / 32];
   __shared__ int s_ok;
   __shared__ volatile int s_fail;
   __shared__ int s_issued;   // units issued by the producer in this generation
@@ -580,14 +584,12 @@ __global__ void __launch_bounds__(kTmaThreads, 1) persist_tma_kernel(const GenPa
           const int64_t rem = p.n_pad - base;
           const int n = (int)(rem < W ? rem : W);
           unsigned char *st_p = stage_mem + (size_t)slot * C::kStageBytes;
-          unsigned char *st_t = st_p + (size_t)W * sizeof(float);
-          SigT *st_a = reinterpret_cast<SigT *>(st_t + (size_t)W * sizeof(float));
+          SigT *st_a = reinterpret_cast<SigT *>(st_p + (size_t)W * sizeof(float));
           SigT *st_b = st_a + W;
           mbar_arrive_expect_tx(&full_bar[slot],
-                                (unsigned)n * (unsigned)(2 * sizeof(float) + 2 * sizeof(SigT)));
+                                (unsigned)n * (unsigned)(sizeof(float) + 2 * sizeof(SigT)));
           bulk_copy_g2s(st_p, p.pool + (int64_t)sl.x * p.n_pad + base, (unsigned)n * 4u,
                         &full_bar[slot]);
-          bulk_copy_g2s(st_t, p.target + base, (unsigned)n * 4u, &full_bar[slot]);
           bulk_copy_g2s(st_a, sig + (int64_t)sl.z * p.n_pad + base, (unsigned)(n * sizeof(SigT)),
                         &full_bar[slot]);
           bulk_copy_g2s(st_b, sig + (int64_t)sl.w * p.n_pad + base, (unsigned)(n * sizeof(SigT)),
@@ -599,11 +601,25 @@ __global__ void __launch_bounds__(kTmaThreads, 1) persist_tma_kernel(const GenPa
       if (!ok) s_fail = 1;
     } else {
       // consumer warps: every warp takes every unit, in order; warp w handles
-      // sub-block w (128 cases) of each chunk, 4 cases per lane, as the
-      // 256-thread CTAs of the other kernels do
+      // sub-block w % 8 (128 cases) of chunks w / 8, w / 8 + 2, ... of each
+      // unit, 4 cases per lane, the same cases per lane as the 256-thread
+      // CTAs of the other kernels; the targets come through L2, requested
+      // before the wait for the unit's rows
+      const int sb = warp & 7, v0 = warp >> 3;
+      constexpr int kMyChunks = (VEC + 1) / 2;   // chunks v0, v0 + 2, ... below VEC
       for (int q = 0; q < nunits && ok; ++q) {
         const unsigned u = u0 + q;
         const int slot = (int)(u % S);
+        const int item = b + q * nb;
+        const int64_t base = (int64_t)(item / m) * W;
+        float4 t4[kMyChunks];
+#pragma unroll
+        for (int c = 0; c < kMyChunks; ++c) {
+          const int jl = (v0 + 2 * c) * 1024 + sb * 128 + lane * 4;
+          t4[c] = make_float4(0.f, 0.f, 0.f, 0.f);
+          if (v0 + 2 * c < VEC && base + jl < p.n_pad)
+            t4[c] = __ldg(reinterpret_cast<const float4 *>(p.target + base + jl));
+        }
         ok = __all_sync(0xffffffffu, mbar_wait(&full_bar[slot], (u / S) & 1u, gs, &s_fail));
         if (!ok) {   // warp-uniform
           s_fail = 1;
@@ -612,25 +628,24 @@ __global__ void __launch_bounds__(kTmaThreads, 1) persist_tma_kernel(const GenPa
         const UnitMeta mt = meta[slot];
         const unsigned char *st_p = stage_mem + (size_t)slot * C::kStageBytes;
         const float *sp = reinterpret_cast<const float *>(st_p);
-        const float *stg = sp + W;
-        const SigT *sa = reinterpret_cast<const SigT *>(stg + W);
-        const SigT *sb = sa + W;
-        const int64_t base = (int64_t)mt.tile * W;
+        const SigT *sa = reinterpret_cast<const SigT *>(sp + W);
+        const SigT *sbb = sa + W;
         float *dst = p.pool + (int64_t)mt.orow * p.n_pad + base;
 #pragma unroll
-        for (int v = 0; v < VEC; ++v) {
-          const int jl = v * 1024 + tid * 4;
+        for (int c = 0; c < kMyChunks; ++c) {
+          const int v = v0 + 2 * c;
+          if (v >= VEC) break;   // warp-uniform
+          const int jl = v * 1024 + sb * 128 + lane * 4;
           float str = 0.f, ste = 0.f;
           if (base + jl < p.n_pad) {
             const float4 s4 = *reinterpret_cast<const float4 *>(sp + jl);
-            const float4 t4 = *reinterpret_cast<const float4 *>(stg + jl);
             float4 a4, b4;
             if (sizeof(SigT) == 4) {
               a4 = *reinterpret_cast<const float4 *>(sa + jl);
-              b4 = *reinterpret_cast<const float4 *>(sb + jl);
+              b4 = *reinterpret_cast<const float4 *>(sbb + jl);
             } else {
               const uint2 ua = *reinterpret_cast<const uint2 *>(sa + jl);
-              const uint2 ub = *reinterpret_cast<const uint2 *>(sb + jl);
+              const uint2 ub = *reinterpret_cast<const uint2 *>(sbb + jl);
               a4 = make_float4(__uint_as_float(ua.x << 16), __uint_as_float(ua.x & 0xffff0000u),
                                __uint_as_float(ua.y << 16), __uint_as_float(ua.y & 0xffff0000u));
               b4 = make_float4(__uint_as_float(ub.x << 16), __uint_as_float(ub.x & 0xffff0000u),
@@ -643,7 +658,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1) persist_tma_kernel(const GenPa
             o.z = fmaf(mt.ms, a4.z - b4.z, s4.z);
             o.w = fmaf(mt.ms, a4.w - b4.w, s4.w);
             *reinterpret_cast<float4 *>(dst + jl) = o;
-            const float dd[4] = {o.x - t4.x, o.y - t4.y, o.z - t4.z, o.w - t4.w};
+            const float dd[4] = {o.x - t4[c].x, o.y - t4[c].y, o.z - t4[c].z, o.w - t4[c].w};
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
               if (j0 + k < p.n_train)
@@ -653,7 +668,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1) persist_tma_kernel(const GenPa
             }
           }
           const float2 sub = subblock_sum(str, ste);
-          if (lane == 0) s_sub[slot][v][warp] = sub;
+          if (lane == 0) s_sub[slot][v][sb] = sub;
         }
         __syncwarp();
         if (lane == 0) mbar_arrive(&empty_bar[slot]);
