@@ -266,8 +266,11 @@ __device__ __forceinline__ void survive_phase(const GenParams &p, const PersistA
   __syncthreads();
 }
 
-template <typename SigT, int VEC, int OPB, bool CROSS>
-__global__ void __launch_bounds__(kGenThreads, 4) persist_kernel(const GenParams p, PersistArgs x) {
+// MINB: CTAs per SM the register budget is sized for (4: 64 registers a
+// thread; 6: 40, the (2, 2) shape, which streams without the one-offspring-
+// ahead pipelining and keeps more warps resident instead).
+template <typename SigT, int VEC, int OPB, bool CROSS, int MINB = 4>
+__global__ void __launch_bounds__(kGenThreads, MINB) persist_kernel(const GenParams p, PersistArgs x) {
   constexpr int NW = kGenThreads / 32;
   constexpr int W = 1024 * VEC;
   __shared__ ItemSums<VEC, OPB> s_sum[2];   // sub-block totals, double-buffered per item
@@ -308,8 +311,8 @@ __global__ void __launch_bounds__(kGenThreads, 4) persist_kernel(const GenParams
     // ---------------- M: mutation stream ----------------------------------
     // CTA b streams items b, b + grid, ... in tile-major order; the grid is
     // sized so that every CTA gets the same number of items.
-    constexpr bool kPipeBf16 = VEC == 2 && !CROSS && std::is_same<SigT, __nv_bfloat16>::value;
-    if constexpr (VEC == 1 || kPipeBf16) {
+    constexpr bool kPipeBf16 = VEC == 2 && !CROSS && std::is_same<SigT, __nv_bfloat16>::value && MINB == 4;
+    if constexpr ((VEC == 1 && MINB == 4) || kPipeBf16) {
       // 1024-case tiles (or bf16 sigma with 2048-case tiles): the draws of
       // each item in shared memory, one item ahead, and the row loads
       // pipelined one offspring ahead
@@ -700,11 +703,12 @@ __global__ void __launch_bounds__(kTmaThreads, 1) persist_tma_kernel(const GenPa
   }
 }
 
-template <typename SigT, int VEC, int OPB>
+template <typename SigT, int VEC, int OPB, int MINB = 4>
 static const void *persist_fn(bool cross) {
-  return cross ? reinterpret_cast<const void *>(&persist_kernel<SigT, VEC, OPB, true>)
-               : reinterpret_cast<const void *>(&persist_kernel<SigT, VEC, OPB, false>);
+  return cross ? reinterpret_cast<const void *>(&persist_kernel<SigT, VEC, OPB, true, MINB>)
+               : reinterpret_cast<const void *>(&persist_kernel<SigT, VEC, OPB, false, MINB>);
 }
+
 
 template <typename SigT, int VEC>
 static const void *persist_tma_fn() {
@@ -721,12 +725,17 @@ struct PersistKernel {
 
 // cross: the register-stream variant with crossover (the TMA variant has none).
 static PersistKernel pick(int bf, const GenShape &sh, bool cross = false) {
+  // (2, 2) is the shape sized for six CTAs per SM (40 registers a thread):
+  // more warps to hide the row loads' latency, fewer loads in flight each
+  if (sh.vec == 2 && sh.opb == 2)
+    return {bf ? persist_fn<__nv_bfloat16, 2, 2, 6>(cross) : persist_fn<float, 2, 2, 6>(cross),
+            kGenThreads, 0};
 #define GSGP_P(V, O)                                                                      \
   if (sh.vec == V && sh.opb == O)                                                         \
     return {bf ? persist_fn<__nv_bfloat16, V, O>(cross) : persist_fn<float, V, O>(cross), \
             kGenThreads, 0};
-  GSGP_P(1, 1) GSGP_P(1, 2) GSGP_P(1, 4) GSGP_P(1, 8) GSGP_P(1, 16) GSGP_P(2, 1) GSGP_P(2, 2)
-  GSGP_P(2, 4) GSGP_P(2, 8)
+  GSGP_P(1, 1) GSGP_P(1, 2) GSGP_P(1, 4) GSGP_P(1, 8) GSGP_P(1, 16) GSGP_P(2, 1) GSGP_P(2, 4)
+  GSGP_P(2, 8)
 #undef GSGP_P
 #define GSGP_T(V)                                                                             \
   if (sh.vec == V && sh.opb == 0)                                                             \
