@@ -414,10 +414,10 @@ gsgp_status gsgp_get_trace(gsgp_ctx *ctx, int32_t g0, int32_t count, int32_t *pa
  *     and replayed from a CUDA graph.
  * Both produce bit-identical results.  The shape of the mutation stream is
  * (vec, opb): a tile of 1024 * vec cases for opb offspring per CTA
- * (persistent: vec in {1,2} with opb in {1,2,4}, vec 1 with opb 8 or 16,
- * or vec 2 with opb 8, streams through registers (with vec 1 the next offspring's rows are
- * loaded while the current one is computed; (2, 2) is sized for six CTAs per
- * SM instead of four), vec in {1,2,4} with opb = 0
+ * (persistent: vec in {1,2} with opb in {1,2,4,8,16} streams through
+ * registers -- with vec 1, and with vec 2 and bf16 sigma, the next
+ * offspring's rows are loaded while the current one is computed; (2, 2) is
+ * sized for six CTAs per SM instead of four --, vec in {1,2,4} with opb = 0
  * stages rows in shared memory with TMA bulk
  * copies, one offspring per unit; chained: vec in {1,2,4}, opb in {2,4,8}).
  * path 0 chooses the path; vec = opb = 0 (the default)

@@ -717,7 +717,7 @@ static gsgp_status launch_generation(gsgp_ctx *c, const GenParams &p, cudaStream
 static const GenShape kChainShapes[] = {{1, 2}, {1, 4}, {1, 8}, {2, 2}, {2, 4},
                                         {2, 8}, {4, 2}, {4, 4}, {4, 8}};
 static const GenShape kPersistShapes[] = {{1, 1}, {1, 2}, {1, 4}, {1, 8}, {1, 16},
-                                          {2, 1}, {2, 2}, {2, 4}, {2, 8}};
+                                          {2, 1}, {2, 2}, {2, 4}, {2, 8}, {2, 16}};
 struct Tuned {
   int path;
   GenShape shape;
@@ -1157,8 +1157,7 @@ extern "C" gsgp_status gsgp_set_evolve_shape(gsgp_ctx *c, int32_t path, int32_t 
     if (path == 0) return fail(c, GSGP_E_INVALID, "a shape needs an explicit path");
     if (path == 1 && !persist_shape_supported(sh))
       return fail(c, GSGP_E_INVALID,
-                  "persistent shape: vec in {1,2} with opb in {1,2,4}, vec 1 with opb 8 or 16, "
-                  "vec 2 with opb 8, "
+                  "persistent shape: vec in {1,2} with opb in {1,2,4,8,16}, "
                   "or vec in {1,2,4} with opb 0");
     if (path == 1 && opb == 0 && c->cfg.p_crossover > 0.0f)
       return fail(c, GSGP_E_INVALID, "the TMA-staged stream does not support crossover");

@@ -735,7 +735,7 @@ static PersistKernel pick(int bf, const GenShape &sh, bool cross = false) {
     return {bf ? persist_fn<__nv_bfloat16, V, O>(cross) : persist_fn<float, V, O>(cross), \
             kGenThreads, 0};
   GSGP_P(1, 1) GSGP_P(1, 2) GSGP_P(1, 4) GSGP_P(1, 8) GSGP_P(1, 16) GSGP_P(2, 1) GSGP_P(2, 4)
-  GSGP_P(2, 8)
+  GSGP_P(2, 8) GSGP_P(2, 16)
 #undef GSGP_P
 #define GSGP_T(V)                                                                             \
   if (sh.vec == V && sh.opb == 0)                                                             \
@@ -751,7 +751,7 @@ static PersistKernel pick(int bf, const GenShape &sh, bool cross = false) {
 
 bool persist_shape_supported(const GenShape &sh) {
   if (sh.opb == 0) return sh.vec == 1 || sh.vec == 2 || sh.vec == 4;
-  return (sh.vec == 1 && (sh.opb == 8 || sh.opb == 16)) || (sh.vec == 2 && sh.opb == 8) ||
+  return ((sh.vec == 1 || sh.vec == 2) && (sh.opb == 8 || sh.opb == 16)) ||
          ((sh.vec == 1 || sh.vec == 2) && (sh.opb == 1 || sh.opb == 2 || sh.opb == 4));
 }
 

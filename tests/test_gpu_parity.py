@@ -329,7 +329,7 @@ def test_device_load_and_torch_allocator():
     (pkg.PATH_CHAINED, 1, 2), (pkg.PATH_CHAINED, 2, 4), (pkg.PATH_CHAINED, 4, 8),
     (pkg.PATH_PERSISTENT, 1, 1), (pkg.PATH_PERSISTENT, 1, 4), (pkg.PATH_PERSISTENT, 1, 8),
     (pkg.PATH_PERSISTENT, 1, 16),
-    (pkg.PATH_PERSISTENT, 2, 2), (pkg.PATH_PERSISTENT, 2, 8),
+    (pkg.PATH_PERSISTENT, 2, 2), (pkg.PATH_PERSISTENT, 2, 8), (pkg.PATH_PERSISTENT, 2, 16),
     (pkg.PATH_PERSISTENT, 1, 0), (pkg.PATH_PERSISTENT, 2, 0), (pkg.PATH_PERSISTENT, 4, 0),
 ])
 def test_every_path_and_shape_gives_identical_results(path, vec, opb):
