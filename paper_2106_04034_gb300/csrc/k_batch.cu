@@ -82,18 +82,30 @@ __global__ void __launch_bounds__(kGenThreads, 4) batch_kernel(const __grid_cons
       };
       if (b < items) stage(b, 0);
       __syncthreads();
-      for (int item = b; item < items; item += nb, buf ^= 1) {
+      // per-run segments of the CTA's items, as below
+      for (int item = b; item < items;) {
         r = advance_run(a.item_off, r, item);
         const GenParams &p = a.runs[r];
         const int groups = (p.m + OPB - 1) / OPB;
+        const int seg_end = a.item_off[r + 1];
+        const int step_t = nb / groups, step_g = nb - step_t * groups;
         const int local = item - a.item_off[r];
-        const int tile = local / groups;
-        const int i0 = (local - tile * groups) * OPB;
-        const int cnt = min(OPB, p.m - i0);
-        if (item + nb < items) stage(item + nb, buf ^ 1);
-        stream_item_pipe<SigT, OPB, CROSS>(p, tile, cnt, s_isel[buf], s_ims[buf], s_sum[buf]);
-        __syncthreads();   // one barrier per item; it also publishes the next item's draws
-        item_partials<VEC, OPB>(p, tile, i0, cnt, s_sum[buf]);
+        int tile = local / groups;
+        int grp = local - tile * groups;
+        for (; item < seg_end; item += nb, buf ^= 1) {
+          const int i0 = grp * OPB;
+          const int cnt = min(OPB, p.m - i0);
+          if (item + nb < items) stage(item + nb, buf ^ 1);
+          stream_item_pipe<SigT, OPB, CROSS>(p, tile, cnt, s_isel[buf], s_ims[buf], s_sum[buf]);
+          __syncthreads();   // one barrier per item; it also publishes the next item's draws
+          item_partials<VEC, OPB>(p, tile, i0, cnt, s_sum[buf]);
+          tile += step_t;
+          grp += step_g;
+          if (grp >= groups) {
+            grp -= groups;
+            ++tile;
+          }
+        }
       }
     } else {
       // the first draws of the next item are loaded one item ahead
@@ -109,20 +121,34 @@ __global__ void __launch_bounds__(kGenThreads, 4) batch_kernel(const __grid_cons
         ms_next = __ldcg(q.sel_ms + i0);
       };
       if (b < items) prefetch(b);
-      for (int item = b; item < items; item += nb, buf ^= 1) {
+      // the CTA's items of one run form a segment: the run's parameters and
+      // its item-to-(tile, offspring group) division are taken once per
+      // segment, and the position advances by nb items without a division
+      for (int item = b; item < items;) {
         r = advance_run(a.item_off, r, item);
         const GenParams &p = a.runs[r];
         const int groups = (p.m + OPB - 1) / OPB;
+        const int seg_end = a.item_off[r + 1];
+        const int step_t = nb / groups, step_g = nb - step_t * groups;
         const int local = item - a.item_off[r];
-        const int tile = local / groups;
-        const int i0 = (local - tile * groups) * OPB;
-        const int cnt = min(OPB, p.m - i0);
-        const int4 sel = sel_next;
-        const float ms = ms_next;
-        if (item + nb < items) prefetch(item + nb);
-        stream_item<SigT, VEC, OPB, CROSS>(p, tile, i0, cnt, sel, ms, s_sum[buf]);
-        __syncthreads();   // one barrier per item (s_sum is double-buffered)
-        item_partials<VEC, OPB>(p, tile, i0, cnt, s_sum[buf]);
+        int tile = local / groups;
+        int grp = local - tile * groups;
+        for (; item < seg_end; item += nb, buf ^= 1) {
+          const int i0 = grp * OPB;
+          const int cnt = min(OPB, p.m - i0);
+          const int4 sel = sel_next;
+          const float ms = ms_next;
+          if (item + nb < items) prefetch(item + nb);
+          stream_item<SigT, VEC, OPB, CROSS>(p, tile, i0, cnt, sel, ms, s_sum[buf]);
+          __syncthreads();   // one barrier per item (s_sum is double-buffered)
+          item_partials<VEC, OPB>(p, tile, i0, cnt, s_sum[buf]);
+          tile += step_t;
+          grp += step_g;
+          if (grp >= groups) {
+            grp -= groups;
+            ++tile;
+          }
+        }
       }
     }
     if (!grid_sync(gs, epoch, &s_ok)) return;
