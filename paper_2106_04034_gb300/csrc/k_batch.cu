@@ -66,23 +66,30 @@ __global__ void __launch_bounds__(kGenThreads, 4) batch_kernel(const __grid_cons
     if (!grid_sync(gs, epoch, &s_ok)) return;
 
     // ---------------- M: mutation stream ----------------------------------
+    // The CTA's items of one run form a segment: the run's parameters and
+    // its item-to-(tile, offspring group) division are taken once per
+    // segment, and the position then advances by nb items without a
+    // division.  The next item's draws are fetched one item ahead: from the
+    // advanced position within the segment, through a run lookup across it.
     if constexpr (VEC == 1) {
       // 1024-case tiles: each item's draws staged in shared memory one item
       // ahead, the row loads pipelined one offspring ahead
       int buf = 0, r = 0, rn = 0;
-      auto stage = [&](int item, int to) {
-        rn = advance_run(a.item_off, rn, item);
-        const GenParams &q = a.runs[rn];
-        const int groups = (q.m + OPB - 1) / OPB;
-        const int i = ((item - a.item_off[rn]) % groups) * OPB + tid;
+      auto stage_from = [&](const GenParams &q, int i0, int to) {
+        const int i = i0 + tid;
         if (tid < OPB && i < q.m) {
           s_isel[to][tid] = __ldcg(q.sel + i);
           s_ims[to][tid] = __ldcg(q.sel_ms + i);
         }
       };
+      auto stage = [&](int item, int to) {   // an item of another run
+        rn = advance_run(a.item_off, rn, item);
+        const GenParams &q = a.runs[rn];
+        const int groups = (q.m + OPB - 1) / OPB;
+        stage_from(q, ((item - a.item_off[rn]) % groups) * OPB, to);
+      };
       if (b < items) stage(b, 0);
       __syncthreads();
-      // per-run segments of the CTA's items, as below
       for (int item = b; item < items;) {
         r = advance_run(a.item_off, r, item);
         const GenParams &p = a.runs[r];
@@ -93,18 +100,21 @@ __global__ void __launch_bounds__(kGenThreads, 4) batch_kernel(const __grid_cons
         int tile = local / groups;
         int grp = local - tile * groups;
         for (; item < seg_end; item += nb, buf ^= 1) {
-          const int i0 = grp * OPB;
+          const int t = tile, i0 = grp * OPB;
           const int cnt = min(OPB, p.m - i0);
-          if (item + nb < items) stage(item + nb, buf ^ 1);
-          stream_item_pipe<SigT, OPB, CROSS>(p, tile, cnt, s_isel[buf], s_ims[buf], s_sum[buf]);
-          __syncthreads();   // one barrier per item; it also publishes the next item's draws
-          item_partials<VEC, OPB>(p, tile, i0, cnt, s_sum[buf]);
           tile += step_t;
           grp += step_g;
           if (grp >= groups) {
             grp -= groups;
             ++tile;
           }
+          if (item + nb < seg_end)
+            stage_from(p, grp * OPB, buf ^ 1);
+          else if (item + nb < items)
+            stage(item + nb, buf ^ 1);
+          stream_item_pipe<SigT, OPB, CROSS>(p, t, cnt, s_isel[buf], s_ims[buf], s_sum[buf]);
+          __syncthreads();   // one barrier per item; it also publishes the next item's draws
+          item_partials<VEC, OPB>(p, t, i0, cnt, s_sum[buf]);
         }
       }
     } else {
@@ -112,7 +122,7 @@ __global__ void __launch_bounds__(kGenThreads, 4) batch_kernel(const __grid_cons
       int buf = 0, r = 0, rn = 0;
       int4 sel_next = make_int4(0, 0, 0, 0);
       float ms_next = 0.f;
-      auto prefetch = [&](int item) {
+      auto prefetch = [&](int item) {   // an item of another run
         rn = advance_run(a.item_off, rn, item);
         const GenParams &q = a.runs[rn];
         const int groups = (q.m + OPB - 1) / OPB;
@@ -121,9 +131,6 @@ __global__ void __launch_bounds__(kGenThreads, 4) batch_kernel(const __grid_cons
         ms_next = __ldcg(q.sel_ms + i0);
       };
       if (b < items) prefetch(b);
-      // the CTA's items of one run form a segment: the run's parameters and
-      // its item-to-(tile, offspring group) division are taken once per
-      // segment, and the position advances by nb items without a division
       for (int item = b; item < items;) {
         r = advance_run(a.item_off, r, item);
         const GenParams &p = a.runs[r];
@@ -134,20 +141,25 @@ __global__ void __launch_bounds__(kGenThreads, 4) batch_kernel(const __grid_cons
         int tile = local / groups;
         int grp = local - tile * groups;
         for (; item < seg_end; item += nb, buf ^= 1) {
-          const int i0 = grp * OPB;
+          const int t = tile, i0 = grp * OPB;
           const int cnt = min(OPB, p.m - i0);
           const int4 sel = sel_next;
           const float ms = ms_next;
-          if (item + nb < items) prefetch(item + nb);
-          stream_item<SigT, VEC, OPB, CROSS>(p, tile, i0, cnt, sel, ms, s_sum[buf]);
-          __syncthreads();   // one barrier per item (s_sum is double-buffered)
-          item_partials<VEC, OPB>(p, tile, i0, cnt, s_sum[buf]);
           tile += step_t;
           grp += step_g;
           if (grp >= groups) {
             grp -= groups;
             ++tile;
           }
+          if (item + nb < seg_end) {
+            sel_next = __ldcg(p.sel + grp * OPB);
+            ms_next = __ldcg(p.sel_ms + grp * OPB);
+          } else if (item + nb < items) {
+            prefetch(item + nb);
+          }
+          stream_item<SigT, VEC, OPB, CROSS>(p, t, i0, cnt, sel, ms, s_sum[buf]);
+          __syncthreads();   // one barrier per item (s_sum is double-buffered)
+          item_partials<VEC, OPB>(p, t, i0, cnt, s_sum[buf]);
         }
       }
     }
