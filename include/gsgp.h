@@ -101,7 +101,12 @@ enum { GSGP_POOL_POPULATION = 0, GSGP_POOL_RANDOM = 1 };
 
 /* Optional device allocator.  alloc returns device memory of at least
  * `bytes` bytes usable on `stream` (NULL on failure -> GSGP_E_OOM); free
- * releases it.  When NULL the library uses cudaMallocAsync/cudaFreeAsync. */
+ * releases it.  When NULL the library allocates stream-ordered
+ * (cudaMallocFromPoolAsync / cudaFreeAsync) from a memory pool the context
+ * creates on its device: memory the context frees (the staging buffers of
+ * gsgp_load and gsgp_predict, the temporaries of gsgp_init) stays mapped in
+ * that pool for its later calls, and the pool with all of its memory goes
+ * at gsgp_destroy. */
 typedef void *(*gsgp_alloc_fn)(void *user, size_t bytes, void *stream);
 typedef void (*gsgp_free_fn)(void *user, void *ptr, void *stream);
 

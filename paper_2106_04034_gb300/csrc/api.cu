@@ -38,6 +38,28 @@ gsgp_status cuda_fail(gsgp_ctx *c, cudaError_t e, const char *what, int line) {
 }
 
 // ---------------------------------------------------------------- memory --
+// Without a caller allocator the context allocates stream-ordered from a
+// pool of its own whose release threshold keeps freed memory: the staging
+// buffers of a load or a prediction and the temporaries of an init are
+// freed at the end of each call, and a pool that returned them to the
+// driver at every synchronisation (the default pool's behaviour) would map
+// fresh physical memory for each call -- measured at 27-33 ms instead of
+// 5 ms for the large workload's 773 MB load once the GPU's memory had been
+// used by other processes.  The pool is destroyed with the context.
+static gsgp_status context_pool(gsgp_ctx *c) {
+  if (c->mem_pool) return GSGP_OK;
+  if (c->device < 0) CK(cudaGetDevice(&c->device));
+  cudaMemPoolProps props{};
+  props.allocType = cudaMemAllocationTypePinned;
+  props.handleTypes = cudaMemHandleTypeNone;
+  props.location.type = cudaMemLocationTypeDevice;
+  props.location.id = c->device;
+  CK(cudaMemPoolCreate(&c->mem_pool, &props));
+  uint64_t keep = ~(uint64_t)0;
+  CK(cudaMemPoolSetAttribute(c->mem_pool, cudaMemPoolAttrReleaseThreshold, &keep));
+  return GSGP_OK;
+}
+
 static gsgp_status dalloc(gsgp_ctx *c, void **p, size_t bytes) {
   *p = nullptr;
   if (bytes == 0) bytes = 16;
@@ -45,7 +67,8 @@ static gsgp_status dalloc(gsgp_ctx *c, void **p, size_t bytes) {
     *p = c->cfg.alloc(c->cfg.alloc_user, bytes, c->stream);
     if (!*p) return fail(c, GSGP_E_OOM, "device allocator returned NULL for %zu bytes", bytes);
   } else {
-    cudaError_t e = cudaMallocAsync(p, bytes, c->stream);
+    TRY(context_pool(c));
+    cudaError_t e = cudaMallocFromPoolAsync(p, bytes, c->mem_pool, c->stream);
     if (e != cudaSuccess) {
       *p = nullptr;
       cudaGetLastError();
@@ -235,6 +258,27 @@ gsgp_status use_device(gsgp_ctx *c) {
   return GSGP_OK;
 }
 
+// Host input of `bytes` bytes to device memory on the context's stream.
+// Page-locked (pinned or registered) host memory that is 16-byte aligned is
+// read by a kernel through its device-mapped address (launch_host_read:
+// no copy-engine stall after long kernels); any other host memory is copied
+// with cudaMemcpyAsync.
+static gsgp_status stage_h2d(gsgp_ctx *c, void *dst, const void *src, size_t bytes) {
+  if (bytes == 0) return GSGP_OK;
+  cudaPointerAttributes at{};
+  if (cudaPointerGetAttributes(&at, src) != cudaSuccess) {
+    cudaGetLastError();   // not a pointer CUDA knows: ordinary host memory
+    at.type = cudaMemoryTypeUnregistered;
+  }
+  if (at.type == cudaMemoryTypeHost && at.devicePointer &&
+      (((uintptr_t)at.devicePointer | (uintptr_t)dst | bytes) & 15u) == 0) {
+    LAUNCH(1, launch_host_read(at.devicePointer, dst, bytes, c->stream));
+  } else {
+    CK(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, c->stream));
+  }
+  return GSGP_OK;
+}
+
 // ------------------------------------------------------------------ load --
 static gsgp_status check_shapes(gsgp_ctx *c, const float *Xtr, const float *ytr, int64_t ntr,
                                 int32_t l, const float *Xte, const float *yte, int64_t nte) {
@@ -303,13 +347,12 @@ extern "C" gsgp_status gsgp_load(gsgp_ctx *c, const float *Xtr, const float *ytr
   } guard{c, stage};
   float *sXtr = stage, *sXte = stage + nx_tr, *sy = stage + nx_tr + nx_te;
   if (ntr > 0) {   // a case shard may hold test cases only
-    CK(cudaMemcpyAsync(sXtr, Xtr, sizeof(float) * nx_tr, cudaMemcpyHostToDevice, c->stream));
-    CK(cudaMemcpyAsync(sy, ytr, sizeof(float) * (size_t)ntr, cudaMemcpyHostToDevice, c->stream));
+    TRY(stage_h2d(c, sXtr, Xtr, sizeof(float) * nx_tr));
+    TRY(stage_h2d(c, sy, ytr, sizeof(float) * (size_t)ntr));
   }
   if (nte > 0) {
-    CK(cudaMemcpyAsync(sXte, Xte, sizeof(float) * nx_te, cudaMemcpyHostToDevice, c->stream));
-    CK(cudaMemcpyAsync(sy + ntr, yte, sizeof(float) * (size_t)nte, cudaMemcpyHostToDevice,
-                       c->stream));
+    TRY(stage_h2d(c, sXte, Xte, sizeof(float) * nx_te));
+    TRY(stage_h2d(c, sy + ntr, yte, sizeof(float) * (size_t)nte));
   }
   if (!c->d_flag) TRY(dalloc_n(c, &c->d_flag, 1));
   CK(cudaMemsetAsync(c->d_flag, 0, sizeof(unsigned), c->stream));
@@ -1458,8 +1501,7 @@ extern "C" gsgp_status gsgp_predict(gsgp_ctx *c, const float *X, int64_t n, doub
   } b{c};
   TRY(dalloc_n(c, &b.Xd, (size_t)n * c->l));
   TRY(dalloc_n(c, &b.yd, (size_t)n));
-  CK(cudaMemcpyAsync(b.Xd, X, sizeof(float) * (size_t)n * c->l, cudaMemcpyHostToDevice,
-                     c->stream));
+  TRY(stage_h2d(c, b.Xd, X, sizeof(float) * (size_t)n * c->l));
   // the cases are checked on the device once copied
   if (!c->d_flag) TRY(dalloc_n(c, &c->d_flag, 1));
   CK(cudaMemsetAsync(c->d_flag, 0, sizeof(unsigned), c->stream));
@@ -1738,6 +1780,7 @@ extern "C" void gsgp_destroy(gsgp_ctx *c) {
     for (auto e : c->ev_init)
       if (e) cudaEventDestroy(e);
     cudaStreamSynchronize(c->stream);
+    if (c->mem_pool) cudaMemPoolDestroy(c->mem_pool);   // every block is back: its memory goes too
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     cudaGetLastError();
   }

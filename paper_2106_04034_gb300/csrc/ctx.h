@@ -18,6 +18,9 @@ struct gsgp_ctx {
   int state = 0;   // 0 created, 1 loaded, 2 initialised
   int device = -1;
   cudaStream_t stream = nullptr;
+  // stream-ordered pool of the context's own device allocations (without a
+  // caller allocator): memory freed by one call stays mapped for the next
+  cudaMemPool_t mem_pool = nullptr;
   cudaStream_t cap_stream = nullptr;
 
   // fitness cases

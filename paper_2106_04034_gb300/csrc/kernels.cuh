@@ -39,6 +39,9 @@ cudaError_t launch_transpose(const float *in, int64_t n, int l, float *out, int6
                              int64_t col0, cudaStream_t s);
 
 cudaError_t launch_nonfinite_check(const float *v, int64_t n, unsigned *flag, cudaStream_t s);
+// Device copy of page-locked host memory by kernel loads (src_mapped: the
+// buffer's device-mapped address); both 16-byte aligned, bytes % 16 == 0.
+cudaError_t launch_host_read(const void *src_mapped, void *dst, size_t bytes, cudaStream_t s);
 
 // mode 0: population (float semantics + per-tile squared errors);
 // mode 1: random trees, sigma stored float; mode 2: sigma stored bf16.
