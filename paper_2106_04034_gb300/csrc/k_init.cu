@@ -458,26 +458,36 @@ __device__ __forceinline__ float logistic(float v) { return 1.0f / (1.0f + expf(
 constexpr int kInterpThreads = 256;
 constexpr int kInterpTile = kInterpThreads * 4;
 
-// One operation on four cases, the operator decided once (warp-uniform).
-__device__ __forceinline__ float4 apply4(int f, const float4 a, const float4 b, float eps) {
-  switch (f) {
-    case kOpAdd: return make_float4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w);
-    case kOpSub: return make_float4(a.x - b.x, a.y - b.y, a.z - b.z, a.w - b.w);
-    case kOpMul: return make_float4(a.x * b.x, a.y * b.y, a.z * b.z, a.w * b.w);
-    default:
-      return make_float4(apply_op(kOpDiv, a.x, b.x, eps), apply_op(kOpDiv, a.y, b.y, eps),
-                         apply_op(kOpDiv, a.z, b.z, eps), apply_op(kOpDiv, a.w, b.w, eps));
+// The values of one stack entry for the thread's VEC chunks (4 cases each).
+template <int VEC>
+struct Lanes {
+  float4 v[VEC];
+};
+
+// One operation on the thread's 4 VEC cases, the operator decided once
+// (warp-uniform).
+template <int F, int VEC>
+__device__ __forceinline__ Lanes<VEC> opv(const Lanes<VEC> &a, const Lanes<VEC> &b, float eps) {
+  Lanes<VEC> r;
+#pragma unroll
+  for (int q = 0; q < VEC; ++q) {
+    const float4 x = a.v[q], y = b.v[q];
+    if (F == kOpAdd)
+      r.v[q] = make_float4(x.x + y.x, x.y + y.y, x.z + y.z, x.w + y.w);
+    else if (F == kOpSub)
+      r.v[q] = make_float4(x.x - y.x, x.y - y.y, x.z - y.z, x.w - y.w);
+    else if (F == kOpMul)
+      r.v[q] = make_float4(x.x * y.x, x.y * y.y, x.z * y.z, x.w * y.w);
+    else
+      r.v[q] = make_float4(apply_op(kOpDiv, x.x, y.x, eps), apply_op(kOpDiv, x.y, y.y, eps),
+                           apply_op(kOpDiv, x.z, y.z, eps), apply_op(kOpDiv, x.w, y.w, eps));
   }
+  return r;
 }
 
-template <int F>
-__device__ __forceinline__ float4 op4(const float4 a, const float4 b, float eps) {
-  return apply4(F, a, b, eps);
-}
-
-// Decoded gene of the interpreter's loop: bits 0-1 the function, bit 2 a
-// terminal operand (alone or fused), bit 3 the terminal is a feature, bit 4
-// a function (alone or fused); the argument is the feature row's offset in
+// Decoded gene, general form: bits 0-1 the function, bit 2 a terminal
+// operand (alone or fused), bit 3 the terminal is a feature, bit 4 a
+// function (alone or fused); the argument is the feature row's offset in
 // float4 units or the constant's bits.
 constexpr int kDecFun = 16, kDecTerm = 4, kDecVar = 8;
 
@@ -489,40 +499,93 @@ __device__ __forceinline__ int2 decode_gene(int g, float c, int64_t row4) {
   return make_int2(code, var ? (int)((g >> 8) * row4) : __float_as_int(c));
 }
 
-// The values of one stack entry for the thread's VEC chunks (4 cases each).
-template <int VEC>
-struct Lanes {
-  float4 v[VEC];
-};
-
-template <int F, int VEC>
-__device__ __forceinline__ Lanes<VEC> opv(const Lanes<VEC> &a, const Lanes<VEC> &b, float eps) {
-  Lanes<VEC> r;
-#pragma unroll
-  for (int q = 0; q < VEC; ++q) r.v[q] = op4<F>(a.v[q], b.v[q], eps);
-  return r;
-}
+// Static form (bits 0-7 of the entry the loop reads; the general code sits in
+// bits 8-15, the stack entry's offset in float4 units in bits 16-31).  The
+// stack depth before every gene of a program is fixed by the program, so the
+// decoding pass resolves it once and the loop keeps no stack pointer:
+//   kStFv + f   top := f(top, feature)        kStFc + f   top := f(top, constant)
+//   kStPop + f  top := f(entry, top)          kStPushV/C  entry := top; top := terminal
+//   kStEnd      the program's end (a sentinel after its last gene)
+constexpr int kStFv = 0, kStFc = 4, kStPop = 8, kStPushV = 12, kStPushC = 13, kStEnd = 14;
 
 // A CTA interprets one program over VEC chunks of 1024 cases: thread t holds
 // cases 4t .. 4t + 3 of each chunk, so one decoded gene serves 4 VEC cases.
 // The stack below the top lives in shared memory as [slot][chunk][thread];
 // each chunk's squared errors are reduced exactly as with one chunk per CTA.
+// Every program the library interprets is well-formed postfix (a generated
+// tree, or the live code of a linear genome), which the static form needs;
+// a program that is not (a function short of operands, or a stack deeper
+// than the launch's slots) is run by the general loop, which tracks the
+// stack pointer and applies the paper's skip rule.
 template <int MODE, int VEC>
-__global__ void __launch_bounds__(kInterpThreads) interpret_kernel(InterpParams p) {
+__global__ void __launch_bounds__(kInterpThreads, 5) interpret_kernel(InterpParams p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float4 *s_stack = reinterpret_cast<float4 *>(smem_raw);
   int2 *s_prog =
       reinterpret_cast<int2 *>(s_stack + (size_t)p.stack_slots * VEC * kInterpThreads);
   __shared__ float2 s_sub[VEC][kInterpThreads / 32];   // sub-block (warp) totals per chunk
+  __shared__ int s_warp[kInterpThreads / 32];
+  __shared__ int s_general;
 
   const int prog = p.order ? p.order[blockIdx.x] : (int)blockIdx.x;
   const int tile = blockIdx.y;
   const int tid = threadIdx.x;
+  const int lane = tid & 31, warp = tid >> 5;
   const int len = p.lengths[prog];
   const int64_t row4 = p.n_pad / 4;   // float4s per feature row
-  for (int k = tid; k < len; k += kInterpThreads)
-    s_prog[k] = decode_gene(p.genes[(size_t)prog * p.K + k], p.consts[(size_t)prog * p.K + k], row4);
+  if (tid == 0) s_general = 0;
+  // Decoding pass: the stack depth before each gene, by a block-wide
+  // prefix sum of the genes' stack effects (+1 terminal, 0 fused,
+  // -1 function).
+  int carry = 0;
+  for (int k0 = 0; k0 < len; k0 += kInterpThreads) {
+    const int k = k0 + tid;
+    int2 d = make_int2(0, 0);
+    int eff = 0;
+    if (k < len) {
+      d = decode_gene(p.genes[(size_t)prog * p.K + k], p.consts[(size_t)prog * p.K + k], row4);
+      eff = (d.x & kDecFun) ? ((d.x & kDecTerm) ? 0 : -1) : 1;
+    }
+    int incl = eff;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int t = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += t;
+    }
+    if (lane == 31) s_warp[warp] = incl;
+    __syncthreads();
+    int before = carry + incl - eff, total = 0;
+#pragma unroll
+    for (int w = 0; w < kInterpThreads / 32; ++w) {
+      const int t = s_warp[w];
+      before += w < warp ? t : 0;
+      total += t;
+    }
+    if (k < len) {
+      int st, slot = 0;
+      bool bad;
+      if (!(d.x & kDecFun)) {   // a terminal alone: the top moves to entry before - 1
+        st = (d.x & kDecVar) ? kStPushV : kStPushC;
+        slot = before > 0 ? before - 1 : 0;
+        bad = before > p.stack_slots;
+      } else if (d.x & kDecTerm) {
+        st = ((d.x & kDecVar) ? kStFv : kStFc) + (d.x & 3);
+        bad = before < 1;
+      } else {
+        st = kStPop + (d.x & 3);
+        slot = before - 2;
+        bad = before < 2;
+      }
+      if (bad) s_general = 1;
+      s_prog[k] =
+          make_int2(st | (d.x << 8) | (bad ? 0 : (slot * VEC * kInterpThreads) << 16), d.y);
+    }
+    carry += total;
+    __syncthreads();   // s_warp is reused
+  }
+  if (tid == 0) s_prog[len] = make_int2(kStEnd, 0);
   __syncthreads();
+  const bool general = s_general != 0;
 
   int64_t j4[VEC];   // float4 index of the thread's cases in chunk q
   bool valid[VEC];
@@ -537,21 +600,6 @@ __global__ void __launch_bounds__(kInterpThreads) interpret_kernel(InterpParams 
   Lanes<VEC> tos;
 #pragma unroll
   for (int q = 0; q < VEC; ++q) tos.v[q] = make_float4(0.f, 0.f, 0.f, 0.f);
-  int sp = 0;
-  auto push = [&](const Lanes<VEC> &x) {
-    if (sp > 0 && sp - 1 < p.stack_slots) {
-#pragma unroll
-      for (int q = 0; q < VEC; ++q) stk[((sp - 1) * VEC + q) * kInterpThreads] = tos.v[q];
-    }
-    tos = x;
-    ++sp;
-  };
-  auto below = [&]() {   // the entry under the top
-    Lanes<VEC> a;
-#pragma unroll
-    for (int q = 0; q < VEC; ++q) a.v[q] = stk[((sp - 2) * VEC + q) * kInterpThreads];
-    return a;
-  };
   auto feature = [&](int off) {
     Lanes<VEC> a;
 #pragma unroll
@@ -564,15 +612,65 @@ __global__ void __launch_bounds__(kInterpThreads) interpret_kernel(InterpParams 
     for (int q = 0; q < VEC; ++q) a.v[q] = make_float4(c, c, c, c);
     return a;
   };
+  auto entry = [&](int off) {   // stack entry at a float4 offset
+    Lanes<VEC> a;
+#pragma unroll
+    for (int q = 0; q < VEC; ++q) a.v[q] = stk[off + q * kInterpThreads];
+    return a;
+  };
+  auto put = [&](int off) {
+#pragma unroll
+    for (int q = 0; q < VEC; ++q) stk[off + q * kInterpThreads] = tos.v[q];
+  };
   const float eps = p.protect_eps;
-  // one jump per gene: every (kind, operator) pair has its own straight-line case
-  for (int k = 0; k < len; ++k) {
-    const int2 e = s_prog[k];
-    switch (e.x) {
+  if (!general) {
+    // one jump per gene over 16 dense codes; the sentinel ends the loop
+    const int2 *pc = s_prog;
+    for (;;) {
+      const int2 e = *pc++;
+      switch (e.x & 15) {
+#define GSGP_ST(F)                                                                       \
+  case kStFv + F:                                                                        \
+    tos = opv<F, VEC>(tos, feature(e.y), eps);                                           \
+    continue;                                                                            \
+  case kStFc + F:                                                                        \
+    tos = opv<F, VEC>(tos, constant(__int_as_float(e.y)), eps);                          \
+    continue;                                                                            \
+  case kStPop + F:                                                                       \
+    tos = opv<F, VEC>(entry(e.x >> 16), tos, eps);                                       \
+    continue;
+        GSGP_ST(kOpAdd)
+        GSGP_ST(kOpSub)
+        GSGP_ST(kOpMul)
+        GSGP_ST(kOpDiv)
+#undef GSGP_ST
+        case kStPushV:
+          put(e.x >> 16);
+          tos = feature(e.y);
+          continue;
+        case kStPushC:
+          put(e.x >> 16);
+          tos = constant(__int_as_float(e.y));
+          continue;
+        default:   // kStEnd
+          break;
+      }
+      break;
+    }
+  } else {
+    int sp = 0;
+    auto push = [&](const Lanes<VEC> &x) {
+      if (sp > 0 && sp - 1 < p.stack_slots) put((sp - 1) * VEC * kInterpThreads);
+      tos = x;
+      ++sp;
+    };
+    for (int k = 0; k < len; ++k) {
+      const int2 e = s_prog[k];
+      switch ((e.x >> 8) & 0xFF) {
 #define GSGP_FUN(F)                                                                      \
   case kDecFun | F:                                                                      \
     if (sp >= 2) {                                                                       \
-      tos = opv<F, VEC>(below(), tos, eps);                                              \
+      tos = opv<F, VEC>(entry((sp - 2) * VEC * kInterpThreads), tos, eps);               \
       --sp;                                                                              \
     }                                                                                    \
     break;                                                                               \
@@ -592,19 +690,20 @@ __global__ void __launch_bounds__(kInterpThreads) interpret_kernel(InterpParams 
       push(v);                                                                           \
     break;                                                                               \
   }
-      GSGP_FUN(kOpAdd)
-      GSGP_FUN(kOpSub)
-      GSGP_FUN(kOpMul)
-      GSGP_FUN(kOpDiv)
+        GSGP_FUN(kOpAdd)
+        GSGP_FUN(kOpSub)
+        GSGP_FUN(kOpMul)
+        GSGP_FUN(kOpDiv)
 #undef GSGP_FUN
-      case kDecTerm:
-        push(constant(__int_as_float(e.y)));
-        break;
-      case kDecTerm | kDecVar:
-        push(feature(e.y));
-        break;
-      default:
-        break;
+        case kDecTerm:
+          push(constant(__int_as_float(e.y)));
+          break;
+        case kDecTerm | kDecVar:
+          push(feature(e.y));
+          break;
+        default:
+          break;
+      }
     }
   }
   // The program's value is register Out (Sec. 2.2, "Interpreter"): every
@@ -613,7 +712,6 @@ __global__ void __launch_bounds__(kInterpThreads) interpret_kernel(InterpParams 
   // function applied), so Out is the final stack top; an empty program is 0.
 
   if (MODE == 0) {
-    const int lane = tid & 31, warp = tid >> 5;
 #pragma unroll
     for (int q = 0; q < VEC; ++q) {
       float str = 0.f, ste = 0.f;
@@ -664,7 +762,7 @@ __global__ void __launch_bounds__(kInterpThreads) interpret_kernel(InterpParams 
 template <int MODE, int VEC>
 static cudaError_t interpret_launch(const InterpParams &p, int count, cudaStream_t s) {
   const size_t smem = (size_t)p.stack_slots * VEC * kInterpThreads * sizeof(float4) +
-                      (size_t)p.max_len * sizeof(int2);
+                      (size_t)(p.max_len + 1) * sizeof(int2);   // genes + the end sentinel
   const int64_t tile = (int64_t)kInterpTile * VEC;
   const dim3 grid((unsigned)count, (unsigned)((p.n_pad + tile - 1) / tile));
   cudaError_t e = cudaFuncSetAttribute(interpret_kernel<MODE, VEC>,

@@ -42,3 +42,32 @@ def test_population_semantics_bit_exact(case):
         assert np.array_equal(S[i].view(np.uint32), want.view(np.uint32)) or \
             np.array_equal(S[i], want, equal_nan=True), i
     run.close()
+
+
+@pytest.mark.parametrize("case", ["deep trees", "genomes k127"])
+def test_population_semantics_bit_exact_extreme_scales(case):
+    """Cases whose features span every exponent (and subnormals): products
+    and quotients overflow, underflow to subnormals and meet the protected
+    division's threshold, with the same bits as a float32 evaluation."""
+    w = CASES[case]
+    Xtr, ytr, Xte, yte = W.make_data(w)
+    rng = np.random.default_rng(20240611)
+
+    def spread(X):
+        k = rng.integers(-140, 128, size=X.shape)
+        return (X.astype(np.float64) * np.exp2(k)).astype(np.float32)
+
+    data = (spread(Xtr), ytr, spread(Xte), yte)
+    assert np.all(np.isfinite(data[0])) and np.all(np.isfinite(data[2]))
+    run, data, p = gpu_run(w, data=data)
+    X = np.ascontiguousarray(np.concatenate([data[0], data[2]]).T, dtype=np.float32)
+    eps = np.float32(p.protect_eps)
+    g, c, L = run.programs(pkg.POOL_POPULATION)
+    S = run.semantics(pkg.POOL_POPULATION)
+    for i in range(len(L)):
+        want = f32_program(g[i, :L[i]], c[i, :L[i]], X, eps)
+        assert np.array_equal(S[i].view(np.uint32), want.view(np.uint32)) or \
+            np.array_equal(S[i], want, equal_nan=True), i
+    run.close()
+
+
