@@ -321,9 +321,9 @@ static gsgp_status prepare_data(gsgp_ctx *c, int64_t ntr, int32_t l, int64_t nte
   c->n_te = nte;
   c->N = N;
   c->n_pad = n_pad;
-  if (!c->X) TRY(dalloc_n(c, &c->X, (size_t)l * n_pad));
+  if (!c->X) TRY(dalloc_n(c, &c->X, (size_t)l * n_pad + kXTailFloats));
   if (!c->t) TRY(dalloc_n(c, &c->t, (size_t)n_pad));
-  CK(cudaMemsetAsync(c->X, 0, sizeof(float) * (size_t)l * n_pad, c->stream));
+  CK(cudaMemsetAsync(c->X, 0, sizeof(float) * ((size_t)l * n_pad + kXTailFloats), c->stream));
   CK(cudaMemsetAsync(c->t, 0, sizeof(float) * (size_t)n_pad, c->stream));
   c->state = 1;
   c->model_gen = -1;

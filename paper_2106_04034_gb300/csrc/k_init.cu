@@ -499,14 +499,147 @@ __device__ __forceinline__ int2 decode_gene(int g, float c, int64_t row4) {
   return make_int2(code, var ? (int)((g >> 8) * row4) : __float_as_int(c));
 }
 
-// Static form (bits 0-7 of the entry the loop reads; the general code sits in
-// bits 8-15, the stack entry's offset in float4 units in bits 16-31).  The
+// Static form (bits 0-3 of the entry the loop reads; the general code sits in
+// bits 4-8, the stack entry's offset in bytes in bits 12-31, i.e. in float4
+// units from bit 16).  The
 // stack depth before every gene of a program is fixed by the program, so the
 // decoding pass resolves it once and the loop keeps no stack pointer:
 //   kStFv + f   top := f(top, feature)        kStFc + f   top := f(top, constant)
 //   kStPop + f  top := f(entry, top)          kStPushV/C  entry := top; top := terminal
 //   kStEnd      the program's end (a sentinel after its last gene)
 constexpr int kStFv = 0, kStFc = 4, kStPop = 8, kStPushV = 12, kStPushC = 13, kStEnd = 14;
+
+// The static loop for two chunks per thread (8 cases) in PTX: the gene's
+// code selects its case by brx.idx.uni and every case returns by bra.uni,
+// both declaring the branch uniform across the warp (every thread of a CTA
+// runs the same program), so no reconvergence bookkeeping surrounds the
+// dispatch.  Arithmetic with explicit round-to-nearest (.rn), so nothing is
+// contracted into an FMA; protected division |b| < eps ? 1 : a / b with
+// IEEE division (div.rn.f32): the same operations, bit for bit, as the
+// general loop.  t[0..7]: the stack top's 8 cases; x0: the thread's first
+// case in feature row 0 for chunk 0 (global; chunk 1 is 4 KB further, read
+// past the last row into the padding of X for a partial last tile, whose
+// values are not stored); pc: the decoded program in shared memory; stk: the
+// thread's stack entry 0, chunk 0 (shared window addresses).  Each case ends
+// by dispatching the next gene.
+#define GSGP_X "%8"
+#define GSGP_EPS "%11"
+#define GSGP_OP_ADD(T, V) "add.rn.f32 " T ", " T ", " V ";\n\t"
+#define GSGP_OP_SUB(T, V) "sub.rn.f32 " T ", " T ", " V ";\n\t"
+#define GSGP_OP_MUL(T, V) "mul.rn.f32 " T ", " T ", " V ";\n\t"
+#define GSGP_OP_DIV(T, V)                                       \
+  "abs.f32 ab, " V ";\n\t"                                      \
+  "setp.lt.f32 pp, ab, " GSGP_EPS ";\n\t"                       \
+  "div.rn.f32 qq, " T ", " V ";\n\t"                            \
+  "selp.f32 " T ", 0f3F800000, qq, pp;\n\t"
+// entry (left operand) op top
+#define GSGP_RP_ADD(T, V) "add.rn.f32 " T ", " V ", " T ";\n\t"
+#define GSGP_RP_SUB(T, V) "sub.rn.f32 " T ", " V ", " T ";\n\t"
+#define GSGP_RP_MUL(T, V) "mul.rn.f32 " T ", " V ", " T ";\n\t"
+#define GSGP_RP_DIV(T, V)                                       \
+  "abs.f32 ab, " T ";\n\t"                                      \
+  "setp.lt.f32 pp, ab, " GSGP_EPS ";\n\t"                       \
+  "div.rn.f32 qq, " V ", " T ";\n\t"                            \
+  "selp.f32 " T ", 0f3F800000, qq, pp;\n\t"
+#define GSGP_ALL8(OP, V0, V1, V2, V3, V4, V5, V6, V7)                                    \
+  OP("%0", V0) OP("%1", V1) OP("%2", V2) OP("%3", V3) OP("%4", V4) OP("%5", V5)         \
+      OP("%6", V6) OP("%7", V7)
+#define GSGP_LOAD_FEATURE                                        \
+  "mad.wide.s32 a0, ey, 16, xg0;\n\t"                            \
+  "ld.global.nc.v4.f32 {v0, v1, v2, v3}, [a0];\n\t"             \
+  "ld.global.nc.v4.f32 {v4, v5, v6, v7}, [a0+4096];\n\t"
+#define GSGP_ENTRY_ADDR                                          \
+  "shr.u32 so, ex, 12;\n\t"                                      \
+  "add.u32 sa, %10, so;\n\t"
+#define GSGP_NEXT                                                \
+  "ld.shared.v2.b32 {ex, ey}, [pcr];\n\t"                        \
+  "add.u32 pcr, pcr, 8;\n\t"                                     \
+  "and.b32 cc, ex, 15;\n\t"                                      \
+  "brx.idx.uni cc, GSGP_TBL;\n\t"
+#define GSGP_CASE_FV(L, OP)                                      \
+  L ":\n\t" GSGP_LOAD_FEATURE GSGP_ALL8(OP, "v0", "v1", "v2", "v3", "v4", "v5", "v6", "v7") \
+  GSGP_NEXT
+#define GSGP_CASE_FC(L, OP)                                      \
+  L ":\n\t" GSGP_ALL8(OP, "ey", "ey", "ey", "ey", "ey", "ey", "ey", "ey") \
+  GSGP_NEXT
+#define GSGP_CASE_POP(L, OP)                                     \
+  L ":\n\t" GSGP_ENTRY_ADDR                                      \
+  "ld.shared.v4.f32 {v0, v1, v2, v3}, [sa];\n\t"                 \
+  "ld.shared.v4.f32 {v4, v5, v6, v7}, [sa+4096];\n\t"            \
+  GSGP_ALL8(OP, "v0", "v1", "v2", "v3", "v4", "v5", "v6", "v7")  \
+  GSGP_NEXT
+
+__device__ __forceinline__ void static_loop_ptx2(Lanes<2> &t, const float4 *x0, unsigned pc,
+                                                 unsigned stk, float eps) {
+  asm volatile(
+      "{\n\t"
+      ".reg .b32 ex, ey, so, sa, pcr;\n\t"
+      ".reg .u32 cc;\n\t"
+      ".reg .b64 a0, xg0;\n\t"
+      ".reg .f32 v0, v1, v2, v3, v4, v5, v6, v7, ab, qq;\n\t"
+      ".reg .pred pp;\n\t"
+      "cvta.to.global.u64 xg0, " GSGP_X ";\n\t"
+      "mov.u32 pcr, %9;\n\t"
+      "GSGP_TBL: .branchtargets GSGP_C0, GSGP_C1, GSGP_C2, GSGP_C3, GSGP_C4, GSGP_C5, GSGP_C6, "
+      "GSGP_C7, GSGP_C8, GSGP_C9, GSGP_C10, GSGP_C11, GSGP_C12, GSGP_C13, GSGP_END, GSGP_END;\n\t"
+      GSGP_NEXT
+      GSGP_CASE_FV("GSGP_C0", GSGP_OP_ADD)
+      GSGP_CASE_FV("GSGP_C1", GSGP_OP_SUB)
+      GSGP_CASE_FV("GSGP_C2", GSGP_OP_MUL)
+      GSGP_CASE_FV("GSGP_C3", GSGP_OP_DIV)
+      GSGP_CASE_FC("GSGP_C4", GSGP_OP_ADD)
+      GSGP_CASE_FC("GSGP_C5", GSGP_OP_SUB)
+      GSGP_CASE_FC("GSGP_C6", GSGP_OP_MUL)
+      GSGP_CASE_FC("GSGP_C7", GSGP_OP_DIV)
+      GSGP_CASE_POP("GSGP_C8", GSGP_RP_ADD)
+      GSGP_CASE_POP("GSGP_C9", GSGP_RP_SUB)
+      GSGP_CASE_POP("GSGP_C10", GSGP_RP_MUL)
+      GSGP_CASE_POP("GSGP_C11", GSGP_RP_DIV)
+      // push a feature: the top goes to its entry, the feature becomes the top
+      "GSGP_C12:\n\t" GSGP_ENTRY_ADDR
+      "st.shared.v4.f32 [sa], {%0, %1, %2, %3};\n\t"
+      "st.shared.v4.f32 [sa+4096], {%4, %5, %6, %7};\n\t"
+      "mad.wide.s32 a0, ey, 16, xg0;\n\t"
+      "ld.global.nc.v4.f32 {%0, %1, %2, %3}, [a0];\n\t"
+      "ld.global.nc.v4.f32 {%4, %5, %6, %7}, [a0+4096];\n\t"
+      GSGP_NEXT
+      // push a constant
+      "GSGP_C13:\n\t" GSGP_ENTRY_ADDR
+      "st.shared.v4.f32 [sa], {%0, %1, %2, %3};\n\t"
+      "st.shared.v4.f32 [sa+4096], {%4, %5, %6, %7};\n\t"
+      "mov.b32 %0, ey;\n\t"
+      "mov.b32 %1, ey;\n\t"
+      "mov.b32 %2, ey;\n\t"
+      "mov.b32 %3, ey;\n\t"
+      "mov.b32 %4, ey;\n\t"
+      "mov.b32 %5, ey;\n\t"
+      "mov.b32 %6, ey;\n\t"
+      "mov.b32 %7, ey;\n\t"
+      GSGP_NEXT
+      "GSGP_END:\n\t"
+      "}"
+      : "+f"(t.v[0].x), "+f"(t.v[0].y), "+f"(t.v[0].z), "+f"(t.v[0].w), "+f"(t.v[1].x),
+        "+f"(t.v[1].y), "+f"(t.v[1].z), "+f"(t.v[1].w)
+      : "l"(x0), "r"(pc), "r"(stk), "f"(eps)
+      : "memory");
+}
+#undef GSGP_CASE_POP
+#undef GSGP_NEXT
+#undef GSGP_CASE_FC
+#undef GSGP_CASE_FV
+#undef GSGP_ENTRY_ADDR
+#undef GSGP_LOAD_FEATURE
+#undef GSGP_ALL8
+#undef GSGP_RP_DIV
+#undef GSGP_RP_MUL
+#undef GSGP_RP_SUB
+#undef GSGP_RP_ADD
+#undef GSGP_OP_DIV
+#undef GSGP_OP_MUL
+#undef GSGP_OP_SUB
+#undef GSGP_OP_ADD
+#undef GSGP_EPS
+#undef GSGP_X
 
 // A CTA interprets one program over VEC chunks of 1024 cases: thread t holds
 // cases 4t .. 4t + 3 of each chunk, so one decoded gene serves 4 VEC cases.
@@ -577,8 +710,10 @@ __global__ void __launch_bounds__(kInterpThreads, 5) interpret_kernel(InterpPara
         bad = before < 2;
       }
       if (bad) s_general = 1;
-      s_prog[k] =
-          make_int2(st | (d.x << 8) | (bad ? 0 : (slot * VEC * kInterpThreads) << 16), d.y);
+      s_prog[k] = make_int2(
+          st | (d.x << 4) |
+              (bad ? 0 : (slot * VEC * kInterpThreads * (int)sizeof(float4)) << 12),
+          d.y);
     }
     carry += total;
     __syncthreads();   // s_warp is reused
@@ -623,7 +758,16 @@ __global__ void __launch_bounds__(kInterpThreads, 5) interpret_kernel(InterpPara
     for (int q = 0; q < VEC; ++q) stk[off + q * kInterpThreads] = tos.v[q];
   };
   const float eps = p.protect_eps;
-  if (!general) {
+  bool done = false;
+  if constexpr (VEC == 2) {
+    if (!general) {
+      static_loop_ptx2(tos, xcase[0], (unsigned)__cvta_generic_to_shared(s_prog),
+                       (unsigned)__cvta_generic_to_shared(stk), eps);
+      done = true;
+    }
+  }
+  if (done) {
+  } else if (!general) {
     // one jump per gene over 16 dense codes; the sentinel ends the loop
     const int2 *pc = s_prog;
     for (;;) {
@@ -666,7 +810,7 @@ __global__ void __launch_bounds__(kInterpThreads, 5) interpret_kernel(InterpPara
     };
     for (int k = 0; k < len; ++k) {
       const int2 e = s_prog[k];
-      switch ((e.x >> 8) & 0xFF) {
+      switch ((e.x >> 4) & 31) {
 #define GSGP_FUN(F)                                                                      \
   case kDecFun | F:                                                                      \
     if (sp >= 2) {                                                                       \

@@ -43,6 +43,11 @@ cudaError_t launch_nonfinite_check(const float *v, int64_t n, unsigned *flag, cu
 // buffer's device-mapped address); both 16-byte aligned, bytes % 16 == 0.
 cudaError_t launch_host_read(const void *src_mapped, void *dst, size_t bytes, cudaStream_t s);
 
+// Floats of padding after the last feature row of X: the interpreter reads
+// the second 1024-case chunk of a tile 4 KB after the first, also past the
+// end of a row for a partial last tile (values it does not use).
+constexpr int kXTailFloats = 1024;
+
 // mode 0: population (float semantics + per-tile squared errors);
 // mode 1: random trees, sigma stored float; mode 2: sigma stored bf16.
 cudaError_t launch_interpret(int mode, const InterpParams &p, int count, cudaStream_t s);
