@@ -510,18 +510,18 @@ __device__ __forceinline__ int2 decode_gene(int g, float c, int64_t row4) {
 constexpr int kStFv = 0, kStFc = 4, kStPop = 8, kStPushV = 12, kStPushC = 13, kStEnd = 14;
 
 // The static loop for two chunks per thread (8 cases) in PTX: the gene's
-// code selects its case by brx.idx.uni and every case returns by bra.uni,
-// both declaring the branch uniform across the warp (every thread of a CTA
-// runs the same program), so no reconvergence bookkeeping surrounds the
-// dispatch.  Arithmetic with explicit round-to-nearest (.rn), so nothing is
-// contracted into an FMA; protected division |b| < eps ? 1 : a / b with
-// IEEE division (div.rn.f32): the same operations, bit for bit, as the
-// general loop.  t[0..7]: the stack top's 8 cases; x0: the thread's first
-// case in feature row 0 for chunk 0 (global; chunk 1 is 4 KB further, read
-// past the last row into the padding of X for a partial last tile, whose
-// values are not stored); pc: the decoded program in shared memory; stk: the
-// thread's stack entry 0, chunk 0 (shared window addresses).  Each case ends
-// by dispatching the next gene.
+// code selects its case by an indirect branch declared uniform across the
+// warp (brx.idx.uni; every thread of a CTA runs the same program), and each
+// case ends with the same dispatch of the next gene, so no reconvergence
+// bookkeeping surrounds it.  Arithmetic with explicit round-to-nearest
+// (.rn), so nothing is contracted into an FMA; protected division
+// |b| < eps ? 1 : a / b with IEEE division (div.rn.f32): the same
+// operations, bit for bit, as the C++ loops.  t[0..7]: the stack top's 8
+// cases; x0: the thread's first case in feature row 0 for chunk 0 (global;
+// chunk 1 is 4 KB further, for a partial last tile read past the last row
+// into the padding of X, values that are not stored); pc: the decoded
+// program in shared memory; stk: the thread's stack entry 0, chunk 0
+// (shared window addresses).
 #define GSGP_X "%8"
 #define GSGP_EPS "%11"
 #define GSGP_OP_ADD(T, V) "add.rn.f32 " T ", " T ", " V ";\n\t"
@@ -758,21 +758,16 @@ __global__ void __launch_bounds__(kInterpThreads, 5) interpret_kernel(InterpPara
     for (int q = 0; q < VEC; ++q) stk[off + q * kInterpThreads] = tos.v[q];
   };
   const float eps = p.protect_eps;
-  bool done = false;
-  if constexpr (VEC == 2) {
-    if (!general) {
+  if (!general) {
+    if constexpr (VEC == 2) {
       static_loop_ptx2(tos, xcase[0], (unsigned)__cvta_generic_to_shared(s_prog),
                        (unsigned)__cvta_generic_to_shared(stk), eps);
-      done = true;
-    }
-  }
-  if (done) {
-  } else if (!general) {
-    // one jump per gene over 16 dense codes; the sentinel ends the loop
-    const int2 *pc = s_prog;
-    for (;;) {
-      const int2 e = *pc++;
-      switch (e.x & 15) {
+    } else {
+      // one jump per gene over 16 dense codes; the sentinel ends the loop
+      const int2 *pc = s_prog;
+      for (;;) {
+        const int2 e = *pc++;
+        switch (e.x & 15) {
 #define GSGP_ST(F)                                                                       \
   case kStFv + F:                                                                        \
     tos = opv<F, VEC>(tos, feature(e.y), eps);                                           \
@@ -783,23 +778,24 @@ __global__ void __launch_bounds__(kInterpThreads, 5) interpret_kernel(InterpPara
   case kStPop + F:                                                                       \
     tos = opv<F, VEC>(entry(e.x >> 16), tos, eps);                                       \
     continue;
-        GSGP_ST(kOpAdd)
-        GSGP_ST(kOpSub)
-        GSGP_ST(kOpMul)
-        GSGP_ST(kOpDiv)
+          GSGP_ST(kOpAdd)
+          GSGP_ST(kOpSub)
+          GSGP_ST(kOpMul)
+          GSGP_ST(kOpDiv)
 #undef GSGP_ST
-        case kStPushV:
-          put(e.x >> 16);
-          tos = feature(e.y);
-          continue;
-        case kStPushC:
-          put(e.x >> 16);
-          tos = constant(__int_as_float(e.y));
-          continue;
-        default:   // kStEnd
-          break;
+          case kStPushV:
+            put(e.x >> 16);
+            tos = feature(e.y);
+            continue;
+          case kStPushC:
+            put(e.x >> 16);
+            tos = constant(__int_as_float(e.y));
+            continue;
+          default:   // kStEnd
+            break;
+        }
+        break;
       }
-      break;
     }
   } else {
     int sp = 0;
