@@ -522,6 +522,9 @@ constexpr int kStFv = 0, kStFc = 4, kStPop = 8, kStPushV = 12, kStPushC = 13, kS
 // into the padding of X, values that are not stored); pc: the decoded
 // program in shared memory; stk: the thread's stack entry 0, chunk 0
 // (shared window addresses).
+// chunk 1 of a thread's cases (feature row, stack entry) is 4096 bytes after chunk 0
+static_assert(kInterpThreads * sizeof(float4) == 4096, "the PTX loop's chunk stride");
+static_assert(kXTailFloats * sizeof(float) >= 4096, "X's padding covers a chunk read past its end");
 #define GSGP_X "%8"
 #define GSGP_EPS "%11"
 #define GSGP_OP_ADD(T, V) "add.rn.f32 " T ", " T ", " V ";\n\t"
