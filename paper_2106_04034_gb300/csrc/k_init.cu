@@ -626,6 +626,87 @@ __device__ __forceinline__ void static_loop_ptx2(Lanes<2> &t, const float4 *x0, 
       : "l"(x0), "r"(pc), "r"(stk), "f"(eps)
       : "memory");
 }
+
+// The same loop for one chunk per thread (4 cases): t[0..3], operands x0,
+// pc, stk, eps as %4 .. %7.
+#define GSGP_OP_DIV1(T, V)                                      \
+  "abs.f32 ab, " V ";\n\t"                                      \
+  "setp.lt.f32 pp, ab, %7;\n\t"                                 \
+  "div.rn.f32 qq, " T ", " V ";\n\t"                            \
+  "selp.f32 " T ", 0f3F800000, qq, pp;\n\t"
+#define GSGP_RP_DIV1(T, V)                                      \
+  "abs.f32 ab, " T ";\n\t"                                      \
+  "setp.lt.f32 pp, ab, %7;\n\t"                                 \
+  "div.rn.f32 qq, " V ", " T ";\n\t"                            \
+  "selp.f32 " T ", 0f3F800000, qq, pp;\n\t"
+#define GSGP_ALL4(OP, V0, V1, V2, V3) OP("%0", V0) OP("%1", V1) OP("%2", V2) OP("%3", V3)
+#define GSGP_ENTRY_ADDR1                                         \
+  "shr.u32 so, ex, 12;\n\t"                                      \
+  "add.u32 sa, %6, so;\n\t"
+#define GSGP_CASE_FV1(L, OP)                                     \
+  L ":\n\t"                                                      \
+  "mad.wide.s32 a0, ey, 16, xg0;\n\t"                            \
+  "ld.global.nc.v4.f32 {v0, v1, v2, v3}, [a0];\n\t"             \
+  GSGP_ALL4(OP, "v0", "v1", "v2", "v3") GSGP_NEXT
+#define GSGP_CASE_FC1(L, OP) L ":\n\t" GSGP_ALL4(OP, "ey", "ey", "ey", "ey") GSGP_NEXT
+#define GSGP_CASE_POP1(L, OP)                                    \
+  L ":\n\t" GSGP_ENTRY_ADDR1                                     \
+  "ld.shared.v4.f32 {v0, v1, v2, v3}, [sa];\n\t"                 \
+  GSGP_ALL4(OP, "v0", "v1", "v2", "v3") GSGP_NEXT
+
+__device__ __forceinline__ void static_loop_ptx1(Lanes<1> &t, const float4 *x0, unsigned pc,
+                                                 unsigned stk, float eps) {
+  asm volatile(
+      "{\n\t"
+      ".reg .b32 ex, ey, so, sa, pcr;\n\t"
+      ".reg .u32 cc;\n\t"
+      ".reg .b64 a0, xg0;\n\t"
+      ".reg .f32 v0, v1, v2, v3, ab, qq;\n\t"
+      ".reg .pred pp;\n\t"
+      "cvta.to.global.u64 xg0, %4;\n\t"
+      "mov.u32 pcr, %5;\n\t"
+      "GSGP_TBL: .branchtargets GSGP_C0, GSGP_C1, GSGP_C2, GSGP_C3, GSGP_C4, GSGP_C5, GSGP_C6, "
+      "GSGP_C7, GSGP_C8, GSGP_C9, GSGP_C10, GSGP_C11, GSGP_C12, GSGP_C13, GSGP_END, GSGP_END;\n\t"
+      GSGP_NEXT
+      GSGP_CASE_FV1("GSGP_C0", GSGP_OP_ADD)
+      GSGP_CASE_FV1("GSGP_C1", GSGP_OP_SUB)
+      GSGP_CASE_FV1("GSGP_C2", GSGP_OP_MUL)
+      GSGP_CASE_FV1("GSGP_C3", GSGP_OP_DIV1)
+      GSGP_CASE_FC1("GSGP_C4", GSGP_OP_ADD)
+      GSGP_CASE_FC1("GSGP_C5", GSGP_OP_SUB)
+      GSGP_CASE_FC1("GSGP_C6", GSGP_OP_MUL)
+      GSGP_CASE_FC1("GSGP_C7", GSGP_OP_DIV1)
+      GSGP_CASE_POP1("GSGP_C8", GSGP_RP_ADD)
+      GSGP_CASE_POP1("GSGP_C9", GSGP_RP_SUB)
+      GSGP_CASE_POP1("GSGP_C10", GSGP_RP_MUL)
+      GSGP_CASE_POP1("GSGP_C11", GSGP_RP_DIV1)
+      // push a feature: the top goes to its entry, the feature becomes the top
+      "GSGP_C12:\n\t" GSGP_ENTRY_ADDR1
+      "st.shared.v4.f32 [sa], {%0, %1, %2, %3};\n\t"
+      "mad.wide.s32 a0, ey, 16, xg0;\n\t"
+      "ld.global.nc.v4.f32 {%0, %1, %2, %3}, [a0];\n\t"
+      GSGP_NEXT
+      // push a constant
+      "GSGP_C13:\n\t" GSGP_ENTRY_ADDR1
+      "st.shared.v4.f32 [sa], {%0, %1, %2, %3};\n\t"
+      "mov.b32 %0, ey;\n\t"
+      "mov.b32 %1, ey;\n\t"
+      "mov.b32 %2, ey;\n\t"
+      "mov.b32 %3, ey;\n\t"
+      GSGP_NEXT
+      "GSGP_END:\n\t"
+      "}"
+      : "+f"(t.v[0].x), "+f"(t.v[0].y), "+f"(t.v[0].z), "+f"(t.v[0].w)
+      : "l"(x0), "r"(pc), "r"(stk), "f"(eps)
+      : "memory");
+}
+#undef GSGP_CASE_POP1
+#undef GSGP_CASE_FC1
+#undef GSGP_CASE_FV1
+#undef GSGP_ENTRY_ADDR1
+#undef GSGP_ALL4
+#undef GSGP_RP_DIV1
+#undef GSGP_OP_DIV1
 #undef GSGP_CASE_POP
 #undef GSGP_NEXT
 #undef GSGP_CASE_FC
@@ -762,44 +843,12 @@ __global__ void __launch_bounds__(kInterpThreads, 5) interpret_kernel(InterpPara
   };
   const float eps = p.protect_eps;
   if (!general) {
-    if constexpr (VEC == 2) {
+    if constexpr (VEC == 2)
       static_loop_ptx2(tos, xcase[0], (unsigned)__cvta_generic_to_shared(s_prog),
                        (unsigned)__cvta_generic_to_shared(stk), eps);
-    } else {
-      // one jump per gene over 16 dense codes; the sentinel ends the loop
-      const int2 *pc = s_prog;
-      for (;;) {
-        const int2 e = *pc++;
-        switch (e.x & 15) {
-#define GSGP_ST(F)                                                                       \
-  case kStFv + F:                                                                        \
-    tos = opv<F, VEC>(tos, feature(e.y), eps);                                           \
-    continue;                                                                            \
-  case kStFc + F:                                                                        \
-    tos = opv<F, VEC>(tos, constant(__int_as_float(e.y)), eps);                          \
-    continue;                                                                            \
-  case kStPop + F:                                                                       \
-    tos = opv<F, VEC>(entry(e.x >> 16), tos, eps);                                       \
-    continue;
-          GSGP_ST(kOpAdd)
-          GSGP_ST(kOpSub)
-          GSGP_ST(kOpMul)
-          GSGP_ST(kOpDiv)
-#undef GSGP_ST
-          case kStPushV:
-            put(e.x >> 16);
-            tos = feature(e.y);
-            continue;
-          case kStPushC:
-            put(e.x >> 16);
-            tos = constant(__int_as_float(e.y));
-            continue;
-          default:   // kStEnd
-            break;
-        }
-        break;
-      }
-    }
+    else
+      static_loop_ptx1(tos, xcase[0], (unsigned)__cvta_generic_to_shared(s_prog),
+                       (unsigned)__cvta_generic_to_shared(stk), eps);
   } else {
     int sp = 0;
     auto push = [&](const Lanes<VEC> &x) {
