@@ -1,6 +1,8 @@
 // Initialisation kernels of Algorithm 1: CreatePopulation (program
 // generation), ComputeSemantics (postfix interpretation over every fitness
 // case) and ComputeFitness of the initial population, plus data staging.
+#include <cstdlib>
+
 #include "kernels.cuh"
 #include "reduce.cuh"
 #include "stream.cuh"
@@ -735,7 +737,8 @@ __device__ __forceinline__ void static_loop_ptx1(Lanes<1> &t, const float4 *x0, 
 // than the launch's slots) is run by the general loop, which tracks the
 // stack pointer and applies the paper's skip rule.
 template <int MODE, int VEC>
-__global__ void __launch_bounds__(kInterpThreads, 5) interpret_kernel(InterpParams p) {
+__global__ void __launch_bounds__(kInterpThreads, 5)
+    interpret_kernel(InterpParams p, int force_general) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float4 *s_stack = reinterpret_cast<float4 *>(smem_raw);
   int2 *s_prog =
@@ -750,7 +753,7 @@ __global__ void __launch_bounds__(kInterpThreads, 5) interpret_kernel(InterpPara
   const int lane = tid & 31, warp = tid >> 5;
   const int len = p.lengths[prog];
   const int64_t row4 = p.n_pad / 4;   // float4s per feature row
-  if (tid == 0) s_general = 0;
+  if (tid == 0) s_general = force_general;
   // Decoding pass: the stack depth before each gene, by a block-wide
   // prefix sum of the genes' stack effects (+1 terminal, 0 fused,
   // -1 function).
@@ -951,6 +954,16 @@ __global__ void __launch_bounds__(kInterpThreads, 5) interpret_kernel(InterpPara
   }
 }
 
+// Diagnostic switch: with the environment variable GSGP_INTERP_GENERAL set
+// to a nonzero integer when gsgp_init runs, every program is interpreted by
+// the general loop (stack pointer, skip rule) instead of the static PTX
+// loop; the results are the same bit for bit.  The library generates only
+// well-formed programs, so this is how the general loop is exercised.
+static int interp_force_general() {
+  const char *v = getenv("GSGP_INTERP_GENERAL");
+  return v && atoi(v) != 0 ? 1 : 0;
+}
+
 template <int MODE, int VEC>
 static cudaError_t interpret_launch(const InterpParams &p, int count, cudaStream_t s) {
   const size_t smem = (size_t)p.stack_slots * VEC * kInterpThreads * sizeof(float4) +
@@ -960,7 +973,7 @@ static cudaError_t interpret_launch(const InterpParams &p, int count, cudaStream
   cudaError_t e = cudaFuncSetAttribute(interpret_kernel<MODE, VEC>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  interpret_kernel<MODE, VEC><<<grid, kInterpThreads, smem, s>>>(p);
+  interpret_kernel<MODE, VEC><<<grid, kInterpThreads, smem, s>>>(p, interp_force_general());
   return cudaGetLastError();
 }
 

@@ -71,3 +71,23 @@ def test_population_semantics_bit_exact_extreme_scales(case):
     run.close()
 
 
+
+
+@pytest.mark.parametrize("case", ["trees", "deep trees", "genomes k1023"])
+def test_general_loop_bit_exact(case, monkeypatch):
+    """The interpreter's general loop (stack pointer and skip rule, for
+    programs that are not well-formed postfix, which the library does not
+    generate) selected by its diagnostic switch: the same bits as a float32
+    evaluation, for one chunk per thread (short trees) and two."""
+    monkeypatch.setenv("GSGP_INTERP_GENERAL", "1")
+    w = CASES[case]
+    run, data, p = gpu_run(w)
+    X = np.ascontiguousarray(np.concatenate([data[0], data[2]]).T, dtype=np.float32)
+    eps = np.float32(p.protect_eps)
+    g, c, L = run.programs(pkg.POOL_POPULATION)
+    S = run.semantics(pkg.POOL_POPULATION)
+    for i in range(len(L)):
+        want = f32_program(g[i, :L[i]], c[i, :L[i]], X, eps)
+        assert np.array_equal(S[i].view(np.uint32), want.view(np.uint32)) or \
+            np.array_equal(S[i], want, equal_nan=True), i
+    run.close()
