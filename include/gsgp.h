@@ -174,8 +174,11 @@ gsgp_status gsgp_load_device(gsgp_ctx *ctx, const float *X_train, const float *y
 /* Initialisation of Algorithm 1: CreatePopulation for P (m programs) and R
  * (r programs), ComputeSemantics of both over all cases (random trees
  * wrapped by the logistic function, Sec. 2), ComputeFitness of P.  Resets
- * the generation counter and the trace.  Errors: GSGP_E_STATE (no data),
- * GSGP_E_OOM, GSGP_E_CUDA. */
+ * the generation counter and the trace.  Diagnostic: with the environment
+ * variable GSGP_INTERP_GENERAL set to a nonzero integer, the interpreter
+ * evaluates every program with its general loop (stack pointer and skip
+ * rule) instead of the precomputed stack schedule; the results are the same
+ * bit for bit.  Errors: GSGP_E_STATE (no data), GSGP_E_OOM, GSGP_E_CUDA. */
 gsgp_status gsgp_init(gsgp_ctx *ctx);
 
 /* Errors of every call that synchronises after device work also include
