@@ -635,7 +635,7 @@ extern "C" gsgp_status gsgp_init(gsgp_ctx *c) {
     CK(cudaMemcpyAsync(need.data(), fz.need, sizeof(int) * need.size(), cudaMemcpyDeviceToHost,
                        c->stream));
     CK(cudaStreamSynchronize(c->stream));
-    static const int kSlotBounds[] = {2, 4, 6, 8, 12, 16, 24, kMaxStack};
+    static const int kSlotBounds[] = {2, 3, 4, 6, 8, 12, 16, 24, kMaxStack};
     for (int q = 0; q < 2; ++q) {
       const int base = q == 0 ? 0 : m, cnt = q == 0 ? m : r;
       int lo = -1;

@@ -736,8 +736,8 @@ __device__ __forceinline__ void static_loop_ptx1(Lanes<1> &t, const float4 *x0, 
 // a program that is not (a function short of operands, or a stack deeper
 // than the launch's slots) is run by the general loop, which tracks the
 // stack pointer and applies the paper's skip rule.
-template <int MODE, int VEC>
-__global__ void __launch_bounds__(kInterpThreads, 5)
+template <int MODE, int VEC, int MINB>
+__global__ void __launch_bounds__(kInterpThreads, MINB)
     interpret_kernel(InterpParams p, int force_general) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float4 *s_stack = reinterpret_cast<float4 *>(smem_raw);
@@ -964,17 +964,28 @@ static int interp_force_general() {
   return v && atoi(v) != 0 ? 1 : 0;
 }
 
-template <int MODE, int VEC>
-static cudaError_t interpret_launch(const InterpParams &p, int count, cudaStream_t s) {
+template <int MODE, int VEC, int MINB>
+static cudaError_t interpret_launch_minb(const InterpParams &p, int count, cudaStream_t s) {
   const size_t smem = (size_t)p.stack_slots * VEC * kInterpThreads * sizeof(float4) +
                       (size_t)(p.max_len + 1) * sizeof(int2);   // genes + the end sentinel
   const int64_t tile = (int64_t)kInterpTile * VEC;
   const dim3 grid((unsigned)count, (unsigned)((p.n_pad + tile - 1) / tile));
-  cudaError_t e = cudaFuncSetAttribute(interpret_kernel<MODE, VEC>,
+  cudaError_t e = cudaFuncSetAttribute(interpret_kernel<MODE, VEC, MINB>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  interpret_kernel<MODE, VEC><<<grid, kInterpThreads, smem, s>>>(p, interp_force_general());
+  interpret_kernel<MODE, VEC, MINB><<<grid, kInterpThreads, smem, s>>>(p, interp_force_general());
   return cudaGetLastError();
+}
+
+// Two chunks per thread with a stack of at most 3 entries below the top
+// (24 KB) leave shared memory for six CTAs per SM: a kernel built for 40
+// registers a thread; otherwise five (48 registers).
+template <int MODE, int VEC>
+static cudaError_t interpret_launch(const InterpParams &p, int count, cudaStream_t s) {
+  if constexpr (VEC == 2) {
+    if (p.stack_slots <= 3) return interpret_launch_minb<MODE, VEC, 6>(p, count, s);
+  }
+  return interpret_launch_minb<MODE, VEC, 5>(p, count, s);
 }
 
 // Pools whose longest program has this many genes take two chunks per CTA
