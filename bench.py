@@ -764,9 +764,12 @@ def time_run(w: W.Workload, data, steps: int = 1, warmup_gens: int = 64):
     e1.record(stream)
     torch.cuda.synchronize()
     kms = run.kernel_times(1 << 22)
+    interp_ms = run.init_kernel_times()          # the last step's two interpreter launches
     run.set_kernel_timing(False)
     ms = e0.elapsed_time(e1) / steps
     info = run.info()
+    gene_cases = float(info.pop_evaluated_genes + info.rt_evaluated_genes) * w.n_cases
+    interp_tops = gene_cases / (float(interp_ms.sum()) / 1e3) / 1e12
     ub = unique_bytes_per_generation(run, w, 2 if w.sigma_bf16 else 4)
     per = info.evolve_generations_per_launch
     bounds = list(range(0, w.generations, per)) + [w.generations]
@@ -777,7 +780,11 @@ def time_run(w: W.Workload, data, steps: int = 1, warmup_gens: int = 64):
     return {"value": float(w.pop_size) * w.n_cases * w.generations / (ms / 1e3), "unit": UNIT,
             "ms_per_step": ms, "steps": steps, "generations": w.generations,
             "stream_frac_of_measured_hbm": achieved / peak,
-            "shape": [info.evolve_tile_cases // 1024, info.evolve_offspring_per_cta]}
+            "shape": [info.evolve_tile_cases // 1024, info.evolve_offspring_per_cta],
+            "interpreter": {"launch_ms": [float(v) for v in interp_ms],
+                            "achieved": interp_tops, "peak": alu_peak_tops(),
+                            "unit": "T lane-ops/s (1 per evaluated gene per case)",
+                            "frac": interp_tops / alu_peak_tops()}}
 
 
 def measure_variants(args):
@@ -786,7 +793,9 @@ def measure_variants(args):
     comparisons are made on one machine: the mid workload (C2); the
     precision variant (large workload, G = 2000, sigma(R) stored bf16)
     against the same run with float32 sigma on the same data (C4); 48
-    batched runs against the same runs evolved one after another (C5)."""
+    batched runs against the same runs evolved one after another (C5); the
+    paper's speed-up shape with genomes of 2047 genes, where the interpreter
+    (ComputeSemantics) takes half of the step."""
     out = {}
     mid = W.MID
     out["mid"] = time_run(mid, W.make_data(mid), steps=3)
@@ -798,6 +807,9 @@ def measure_variants(args):
     out["large_bf16"] = {"workload": W.LARGE_BF16.name, "bf16_sigma": bf16, "f32_sigma": f32,
                          "speedup_bf16_over_f32": bf16["value"] / f32["value"]}
     del data
+    pk = W.PAPER_K2047
+    out["paper_k2047"] = time_run(pk, W.make_data(pk))
+    out["paper_k2047"]["workload"] = pk.name
     bargs = argparse.Namespace(**vars(args))
     bargs.steps, bargs.warmup, bargs.shape, bargs.generations = 1, 1, "", 0
     bargs.skip_e2e = True
