@@ -424,19 +424,39 @@ def run_batched(args, rank, world, local_rank):
             r.best_trace()
             r.predict_device(d[2], y)
 
+    # CUDA events around the evolution alone (the per-run staging, init and
+    # finishing are the same work in both forms)
+    evolve_ev = {"batched": [], "sequential": []}
+
+    def mark():
+        e = torch.cuda.Event(enable_timing=True)
+        e.record(stream)
+        return e
+
     def step():
         for r, d in zip(runs, devs):
             r.load_device(*d)
             r.init()
+        e = mark()
         batch.evolve(G, log=False)
+        evolve_ev["batched"].append([(e, mark())])
         finish()
 
     def step_sequential():
+        pairs = []
         for r, d in zip(runs, devs):
             r.load_device(*d)
             r.init()
+            e = mark()
             r.evolve(G, log=False)
+            pairs.append((e, mark()))
+        evolve_ev["sequential"].append(pairs)
         finish()
+
+    def evolve_ms(kind, steps):
+        torch.cuda.synchronize()
+        last = evolve_ev[kind][-steps:]
+        return sum(a.elapsed_time(b) for pairs in last for a, b in pairs) / len(last)
 
     def barrier():
         if world > 1:
@@ -489,6 +509,8 @@ def run_batched(args, rank, world, local_rank):
     seq_steps = max(1, min(args.steps, 2))
     ms_seq = timed(step_sequential, seq_steps)
     value_seq = job_value(updates, world, ms_seq / 1e3)
+    evolve_batched_ms = evolve_ms("batched", args.steps)
+    evolve_sequential_ms = evolve_ms("sequential", seq_steps)
 
     # end to end through host buffers (pinned host memory)
     hdatas = [[torch.from_numpy(a).pin_memory().numpy() for a in d] for d in datas]
@@ -536,6 +558,10 @@ def run_batched(args, rank, world, local_rank):
         "sequential": {"value": value_seq, "unit": UNIT, "ms_per_step": ms_seq,
                        "steps": seq_steps,
                        "what": "the same runs one after another through gsgp_evolve"},
+        "evolve_only": {"batched_ms": evolve_batched_ms, "sequential_ms": evolve_sequential_ms,
+                        "speedup": evolve_sequential_ms / evolve_batched_ms,
+                        "what": "CUDA-event time of batch.evolve(G) against the sum of the "
+                                "runs' gsgp_evolve(G), within the same timed steps"},
         "roofline": {"kernel": "batch_kernel", "bound": "hbm", "achieved": achieved,
                      "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": None,
@@ -819,6 +845,7 @@ def measure_variants(args):
                       "sequential": line["sequential"],
                       "speedup_batched_over_sequential":
                           line["value"] / line["sequential"]["value"],
+                      "evolve_only": line["evolve_only"],
                       "stream_frac_of_measured_hbm": line["roofline"]["frac"],
                       "shape": line["roofline"]["shape"]}
     return out
