@@ -816,13 +816,17 @@ def time_run(w: W.Workload, data, steps: int = 1, warmup_gens: int = 64):
 def measure_variants(args):
     """The other workloads of the benchmark on the same GPU as the headline
     (one timed step each after an untimed autotuning warm-up), so that their
-    comparisons are made on one machine: the mid workload (C2); the
+    comparisons are made on one machine: the tiny workload (C1, latency-
+    bound, 20 steps); the mid workload (C2); the
     precision variant (large workload, G = 2000, sigma(R) stored bf16)
     against the same run with float32 sigma on the same data (C4); 48
     batched runs against the same runs evolved one after another (C5); the
     paper's speed-up shape with genomes of 2047 genes, where the interpreter
     (ComputeSemantics) takes half of the step."""
     out = {}
+    tiny = W.TINY
+    out["tiny"] = time_run(tiny, W.make_data(tiny), steps=20)
+    out["tiny"]["workload"] = tiny.name
     mid = W.MID
     out["mid"] = time_run(mid, W.make_data(mid), steps=3)
     out["mid"]["workload"] = mid.name
