@@ -735,7 +735,9 @@ __device__ __forceinline__ void static_loop_ptx1(Lanes<1> &t, const float4 *x0, 
 // tree, or the live code of a linear genome), which the static form needs;
 // a program that is not (a function short of operands, or a stack deeper
 // than the launch's slots) is run by the general loop, which tracks the
-// stack pointer and applies the paper's skip rule.
+// stack pointer and skips a function short of operands (the paper's rule);
+// its value is then the final stack top (register Out is the live code's
+// root, which compaction has already made the last gene).
 template <int MODE, int VEC, int MINB>
 __global__ void __launch_bounds__(kInterpThreads, MINB)
     interpret_kernel(InterpParams p, int force_general) {
