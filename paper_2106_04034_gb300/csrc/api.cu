@@ -619,8 +619,9 @@ extern "C" gsgp_status gsgp_init(gsgp_ctx *c) {
   // Interpreter launches: one per group of programs, shared memory sized for
   // the group's deepest stack.  Linear genomes are grouped by the stack
   // entries each needs (most need a few; the deepest of a large pool needs
-  // about twice as many, and sizing every CTA for it costs occupancy); a
-  // pool of trees is one group sized by its depth.
+  // about twice as many, and sizing every CTA for it costs occupancy; a
+  // group needing at most 3 also runs at six CTAs per SM instead of five);
+  // a pool of trees is one group sized by its depth.
   struct Group {
     int first, count, slots;   // first < 0: programs 0 .. count - 1 in order
   };
